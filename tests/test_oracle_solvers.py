@@ -1,0 +1,120 @@
+"""Pins of the oracle's Krylov solvers, Newton and Chebyshev-preconditioned Arnoldi.
+
+* BiCGstab(2) and GMRES reproduce a dense LAPACK solve.
+* The Chebyshev filter equals T_n((z-d)/c) / T_n((lam_ref-d)/c) evaluated by
+  numpy's Chebyshev-series routine, for real and imaginary focal distances.
+* At Gr = 0 about conduction, J is block triangular and the leading
+  eigenvalues are the closed-form temperature-block values
+  -(1/Pr) sum_d 4 n_d^2 sin^2(k_d pi / 2 n_d) (Dirichlet in x, Neumann in y, z).
+* At Gr > 0 the Arnoldi eigenvalues match a dense eigen-solve of P J restricted
+  to an orthonormal basis of the divergence-free subspace.
+* Newton converges quadratically to a state with P F = 0, D u = 0, and the
+  three symmetry measures of Eqs. 7-9 at round-off (the paper quotes "order
+  1e-9" for symmetric solutions, Section 2).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle.discretisation as D
+from oracle import diagnostics as DG
+from oracle import solvers as SV
+from oracle.projection import Projector
+from paper_2210_08816_gb300 import seeded
+
+PR = 0.71
+
+
+def test_krylov_solvers_match_dense_solve():
+    n = 60
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((n, n)) / np.sqrt(n) + 3.0 * np.eye(n)
+    b = rng.standard_normal(n)
+    ref = np.linalg.solve(A, b)
+    for f in (SV.bicgstab2, SV.gmres):
+        x, info = f(lambda v: A @ v, b, tol=1e-12)
+        assert info["status"] == "converged"
+        assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("c2", [2.5, -1.7, 0.0])
+def test_chebyshev_filter_is_scaled_chebyshev_polynomial(c2):
+    lam = np.linspace(-9.0, -1.0, 17)
+    d, lam_ref, n = -5.0, 0.3, 23
+    y = SV.chebyshev_filter(lambda v: lam * v, np.ones_like(lam), d, c2, lam_ref, n)
+    if c2 == 0.0:
+        expect = ((lam - d) / (lam_ref - d)) ** n
+    else:
+        c = np.sqrt(complex(c2))
+        coef = np.zeros(n + 1)
+        coef[n] = 1.0
+        Tn = lambda z: np.polynomial.chebyshev.chebval(z, coef)
+        expect = (Tn((lam - d) / c) / Tn((lam_ref - d) / c)).real
+    assert np.allclose(y, expect, rtol=1e-10, atol=1e-14)
+
+
+def _temperature_block(nx, ny, nz, k):
+    l1 = lambda n, j: 4.0 * n * n * np.sin(j * np.pi / (2 * n)) ** 2
+    vals = sorted((-(l1(nx, a) + l1(ny, b) + l1(nz, c)) / PR
+                   for a in range(1, 4) for b in range(0, 4) for c in range(0, 4)), reverse=True)
+    return np.array(vals[:k])
+
+
+def test_arnoldi_gr0_closed_form_temperature_spectrum():
+    g = D.Grid(10, 8, 6, stretch=0.0, Pr=PR)
+    q = D.conduction_state(g)
+    x0 = seeded.normal(1, 0, D.n_unknowns(g))
+    lam, X, info = SV.leading_eigenvalues(g, 0.0, q, k=4, m=20, seed_vector=x0, tol=1e-10)
+    assert info["converged"]
+    expect = _temperature_block(10, 8, 6, 4)
+    assert np.allclose(lam.real, expect, rtol=1e-9, atol=0)
+    assert np.all(np.abs(lam.imag) <= 1e-9 * np.abs(lam.real))
+
+
+def _dense_restricted(g, Gr, q):
+    """Z^T (P J) Z on an orthonormal basis Z of {D u = 0} x {T}."""
+    n = D.n_unknowns(g)
+    nt = g.nx * g.ny * g.nz
+    nv = n - nt
+    Dm = np.zeros((nt, nv))
+    for i in range(nv):
+        e = np.zeros(n)
+        e[i] = 1.0
+        Dm[:, i] = D.divergence_full(g, D.unpack(g, e)[:3]).ravel()
+    Zv = sla.null_space(Dm)
+    Z = np.zeros((n, Zv.shape[1] + nt))
+    Z[:nv, :Zv.shape[1]] = Zv
+    Z[nv:, Zv.shape[1]:] = np.eye(nt)
+    A = SV.projected_jacobian(g, Gr, q)
+    AZ = np.stack([A(Z[:, i]) for i in range(Z.shape[1])], axis=1)
+    lam = np.linalg.eigvals(Z.T @ AZ)
+    return lam[SV.order_eigs(lam)], Z
+
+
+def test_newton_then_arnoldi_match_dense_eigensolve():
+    g = D.Grid(8, 7, 6, stretch=1.5, Pr=PR)
+    Gr = 1.2e4
+    q, rep = SV.newton_steady(g, Gr, D.conduction_state(g), tol=1e-11)
+    assert rep["status"] == "converged"
+    res = rep["residual"]
+    assert res[-1] <= 1e-11 * res[0]
+    # quadratic convergence: the last contraction is much stronger than the first
+    assert res[-1] / res[-2] < 1e-2 * (res[1] / res[0])
+    assert np.max(np.abs(D.divergence_full(g, q[:3]))) <= 1e-10 * max(np.max(np.abs(q[c])) for c in range(3)) / 0.01
+    # the steady state keeps the three symmetries of Section 2
+    assert max(DG.symmetry_measures(g, q[3])) <= 1e-9
+    assert DG.nusselt_hot(g, q[3]) < -1.0
+    lam_dense, _ = _dense_restricted(g, Gr, q)
+    x0 = seeded.normal(2, 0, D.n_unknowns(g))
+    lam, X, info = SV.leading_eigenvalues(g, Gr, q, k=4, m=20, seed_vector=x0, tol=1e-9)
+    assert info["converged"]
+    k = len(lam)
+    assert np.allclose(lam, lam_dense[:k], rtol=1e-8, atol=0), (lam, lam_dense[:k + 2])
+
+
+def test_conduction_nusselt_and_energy():
+    g = D.Grid(9, 7, 5, stretch=1.5, Pr=PR)
+    q = D.conduction_state(g)
+    assert DG.nusselt_hot(g, q[3]) == pytest.approx(-1.0, rel=1e-13)    # Eq. 13 as printed
+    assert DG.kinetic_energy(g, q) == 0.0
+    assert DG.symmetry_measures(g, q[3]) == (0.0, 0.0, 0.0)
