@@ -1,0 +1,472 @@
+"""Throughput of the J.v + projection hot path on the 256^3 tanh-stretched cube at Gr = 2e8.
+
+One step = one Chebyshev-filter step of the Arnoldi iteration on a 256^3 FP32 Krylov vector:
+    y_next = alpha (P (J(q) y - sigma y) + sigma y) + beta y + gamma y_prev      (J.v, divergence,
+             fast-diagonalisation pressure solve, gradient correction with the recurrence fused)
+followed by its FP64 inner product <y_next, y_next> (read back to the host).  The metric counts one
+J.v + projection per step.  Inputs (base state q, Krylov vectors) are seeded synthetic fields of the
+paper's workload shape; every buffer (268 MB per FP32 vector) is larger than the 129 MB L2.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (the reference
+arm: there is no reference code, only the paper).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J.v+projection/s at 256^3 (HBM %); time-to-leading-eigenpair vs plain FP64 @1e-6"
+UNIT = "J.v+projection/s"
+NX = NY = NZ = 256
+STRETCH, GR, PR = 1.5, 2.0e8, 0.71
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=256)
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    p.add_argument("--no-eigen", action="store_true", help="skip the 32^3 time-to-eigenpair leg")
+    p.add_argument("--cpu-sample-only", action="store_true", help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed (replicas)
+def dist_setup(n):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def max_over_ranks(ws, x, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(n, device):
+    """Base state q = conduction + N(0, 50^2) seeded perturbation, projected by the library (FP64);
+    Krylov vectors y0, y1: seeded N(0,1).  Host generation (SplitMix64 + Box-Muller), then upload."""
+    import numpy as np
+    import torch
+    from paper_2210_08816_gb300 import fv, seeded
+    g = fv.Grid(n, n, n, stretch=STRETCH, Pr=PR)
+    shape = (n, n, n)
+
+    def to_dev(fields, dtype):
+        return torch.from_numpy(np.stack(fields)).to(device=device, dtype=dtype).contiguous().view(-1)
+
+    q = to_dev(seeded.normal_fields(100, shape, 50.0), torch.float64)
+    fv.fv_project(g, fv.FV_FP64, q)          # divergence-free perturbation (wall slots zeroed inside)
+    xf = np.array(g_faces(n))
+    xc = 0.5 * (xf[:-1] + xf[1:])
+    T = q.view(4, n, n, n)[3]
+    T += torch.from_numpy(1.0 - xc).to(device)[None, None, :]
+    y0 = to_dev(seeded.normal_fields(101, shape), torch.float64)
+    y1 = to_dev(seeded.normal_fields(102, shape), torch.float64)
+    fv.fv_project(g, fv.FV_FP64, y0)
+    fv.fv_project(g, fv.FV_FP64, y1)
+    return g, q, y0, y1
+
+
+def g_faces(n):
+    import math
+    f = [0.5 * (1.0 + math.tanh(STRETCH * (2.0 * i / n - 1.0)) / math.tanh(STRETCH)) for i in range(n + 1)]
+    for k in range(n // 2 + 1):
+        f[n - k] = 1.0 - f[k]
+    if n % 2 == 0:
+        f[n // 2] = 0.5
+    f[0], f[n] = 0.0, 1.0
+    return f
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_steps(fv, g, prec, q, ya, yb, K, stream, sigma, profile=False):
+    """K recurrence steps y_{j+1} = 2 t (A - d) y_j - c2 t t' y_{j-1} (fixed coefficients of a
+    degree-K Chebyshev filter on [-2|sigma|, 0]) + FP64 norm read-back; returns (ms, last norm)."""
+    import torch
+    d, c2 = sigma, sigma * sigma * 0.9
+    s = 10.0 - d
+    tau = 1.0 / s
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    if profile:
+        fv.fv_profile(g, True)
+    start.record(stream)
+    nrm = 0.0
+    for _ in range(K):
+        tn = 1.0 / (2.0 * s - c2 * tau)
+        # yb <- 2 tn (A - d) ya - c2 tau tn yb   (A = P(J - sigma) + sigma)
+        fv.fv_jvp_project_lincomb(g, prec, GR, sigma, q, ya, yb, 2.0 * tn, -2.0 * tn * d, -c2 * tau * tn, yb)
+        nrm = fv.fv_dot(g, prec, yb, yb)
+        if nrm > 1e30 or nrm < 1e-30:
+            sc = 1.0 / nrm ** 0.5
+            fv.fv_axpby(g, prec, 0.0, yb, sc, yb)
+            fv.fv_axpby(g, prec, 0.0, ya, sc, ya)
+        ya, yb = yb, ya
+        tau = tn
+    stop.record(stream)
+    stop.synchronize()
+    prof = fv.fv_profile_read(g) if profile else None
+    if profile:
+        fv.fv_profile(g, False)
+    return start.elapsed_time(stop), nrm, prof, ya, yb
+
+
+def gpu_arm(args, ws, rank, local):
+    import torch
+    from paper_2210_08816_gb300 import build, fv
+    build.build()
+    fv.lib()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream()
+    n = args.grid
+    g, q64, y0_64, y1_64 = make_inputs(n, device)
+    sigma = -0.5 * (1.0 / PR) * 3 * 4.0 / (min(b - a for a, b in zip(g_faces(n)[:-1], g_faces(n)[1:])) ** 2)
+    # FP32 copies (the mixed form's Krylov vectors and base state)
+    q = q64.float()
+    ya, yb = y0_64.float(), y1_64.float()
+    N = n * n * n
+    W, K = max(3, args.warmup), args.steps
+    run_steps(fv, g, fv.FV_FP32, q, ya, yb, W, stream, sigma)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, nrm, prof, ya, yb = run_steps(fv, g, fv.FV_FP32, q, ya, yb, K, stream, sigma, profile=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(ws, ms, device)
+    ms_step = ms / K
+    value = ws * K / (ms / 1e3)
+    launches = sum(c for _, c in prof.values())
+
+    # roofline of the dominant kernel class
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    clocks = clk.summary()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if dom == "transform":
+        flops = 2.0 * N * n                               # one n x n matrix along one axis of an N-cell field
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"kernel": "k_transform<float> (fast-diagonalisation transform)", "bound": "alu",
+                "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "peak_source": "FP32 FMA lanes x 2 x 152 SMs x 2070 MHz (unit counts and max clock)"}
+        traffic_bytes = 2 * N * 4
+    else:
+        bytes_per = {"stencil": 12 * N * 4, "correct": 9 * N * 4, "divergence": 4 * N * 4}.get(dom, 2 * 4 * N * 4)
+        achieved = bytes_per / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_source": hbm_src}
+        traffic_bytes = bytes_per
+    roof["traffic"] = measured_traffic(dom, n)
+    roof["algorithmic_bytes"] = traffic_bytes
+    roof["launch_ms"] = round(per_launch_ms, 4)
+    st_ms, st_n = prof["stencil"]
+    st_gbs = 12 * N * 4 / (st_ms / st_n * 1e-3) / 1e9
+    hbm_stencil = {"kernel": "k_stencil<float,1> (J.v)", "achieved": round(st_gbs, 1), "peak": hbm_peak,
+                   "unit": "GB/s", "frac": round(st_gbs / hbm_peak, 4), "algorithmic_bytes": 12 * N * 4,
+                   "launch_ms": round(st_ms / st_n, 4)}
+    step_bytes = (12 + 1 + 2 * 6 + 1 + 11) * N * 4   # stencil, divergence, 6 transforms r+w, correction, dot
+    breakdown = {k: {"ms_per_step": round(v[0] / K, 4), "launches_per_step": v[1] / K} for k, v in prof.items()}
+
+    # e2e through the C-ABI with host buffers: H2D of the step's input vector, the step, D2H of the result
+    host_in = ya.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ke = max(3, min(K, 10))
+    for _ in range(2):
+        ya.copy_(host_in, non_blocking=True)
+        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb)
+        host_out.copy_(yb, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    e0.record(stream)
+    for _ in range(Ke):
+        ya.copy_(host_in, non_blocking=True)
+        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb)
+        host_out.copy_(yb, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e_ms = max_over_ranks(ws, e0.elapsed_time(e1), device)
+    e2e = {"value": round(ws * Ke / (e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": host_in.numel() * 4,
+           "d2h_bytes_per_step": host_out.numel() * 4, "steps": Ke}
+    del host_in, host_out
+
+    # plain FP64 form on the same GPU (same step, FP64 everywhere)
+    za, zb = y0_64.clone(), y1_64.clone()
+    run_steps(fv, g, fv.FV_FP64, q64, za, zb, 2, stream, sigma)
+    K64 = max(3, min(K, 5))
+    ms64, _, _, _, _ = run_steps(fv, g, fv.FV_FP64, q64, za, zb, K64, stream, sigma)
+    ms64 = max_over_ranks(ws, ms64, device)
+    fp64 = {"value": round(ws * K64 / (ms64 / 1e3), 3), "ms_per_step": round(ms64 / K64, 3), "steps": K64}
+    del za, zb
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 tanh-stretched (s=1.5) cube, Gr=2e8, Pr=0.71: one Chebyshev-filter step "
+                               "(J.v + fast-diagonalisation projection + fused recurrence) + FP64 norm",
+                   "grid": [n, n, n], "stretch": STRETCH, "Gr": GR, "Pr": PR, "precision": "mixed (FP32 vectors, "
+                   "FP64 reductions)", "poisson": "direct fast diagonalisation (I_p = 1)",
+                   "l2": "inputs larger than L2 (268 MB per FP32 vector vs 129 MB L2)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "hbm_stencil": hbm_stencil,
+        "step_algorithmic_bytes": step_bytes, "kernel_breakdown": breakdown, "fp64_plain": fp64,
+        "clocks": clocks,
+    }
+    del q, ya, yb, q64, y0_64, y1_64
+    g.close()
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_eigen:
+        result["time_to_eigenpair"] = eigen_leg(fv, device)
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(n)
+    return result
+
+
+def measured_traffic(kind, n):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kind)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2210_08816_gb300", "csrc", rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != rec.get("sha") or rec.get("grid") != n:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def eigen_leg(fv, device):
+    """Time to the leading eigenpairs (k = 4, m = 20, 1e-6) at 32^3 uniform, Gr = 1e5, from the Newton
+    steady state: plain FP64 vs mixed, same GPU."""
+    import numpy as np
+    import torch
+    n, Gr = 32, 1.0e5
+    g = fv.Grid(n, n, n, stretch=0.0, Pr=PR)
+    x = (np.arange(n) + 0.5) / n
+    q = torch.zeros(4, n, n, n, dtype=torch.float64, device=device)
+    q[3] = torch.from_numpy(1.0 - x).to(device)[None, None, :]
+    q = q.view(-1).contiguous()
+    o = fv.fv_newton_default_opts()
+    o.gr_start, o.gr_ratio = 1.25e4, 2.0
+    t0 = time.time()
+    st, rep = fv.newton_steady(g, Gr, q, o)
+    torch.cuda.synchronize()
+    t_newton = time.time() - t0
+    out = {"workload": "32^3 uniform, Gr=1e5, k=4, m=20, tol 1e-6", "newton_s": round(t_newton, 3),
+           "newton_status": st, "newton_matvecs": rep.matvecs}
+    lam = {}
+    for name, prec in (("fp64", fv.FV_FP64), ("mixed", fv.FV_FP32)):
+        a = fv.fv_arnoldi_default_opts()
+        a.precision, a.tol = prec, 1e-6
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st, l, r = fv.arnoldi_leading(g, 4, Gr, q, a)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": round(time.time() - t0, 3), "status": st, "matvecs": r.matvecs,
+                     "restarts": r.restarts, "lambda1": [l[0].real, l[0].imag] if l else None}
+        lam[name] = l[0] if l else None
+    if lam.get("fp64") is not None and lam.get("mixed") is not None:
+        out["lambda1_rel_diff"] = abs(lam["mixed"] - lam["fp64"]) / abs(lam["fp64"])
+    g.close()
+    return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_step_seconds(n, reps=1):
+    """Time `reps` oracle J.v + projections (FP64 numpy) on the n^3 workload; returns seconds per step."""
+    import numpy as np
+    import oracle.discretisation as D
+    from oracle.projection import Projector
+    from paper_2210_08816_gb300 import seeded
+    og = D.Grid(n, n, n, stretch=STRETCH, Pr=PR)
+    P = Projector(og)
+    q = D.from_api(og, seeded.normal_fields(100, og.shape, 50.0))
+    q[3] = q[3] + (1.0 - og.axes[0].xc)[None, None, :]
+    v = D.from_api(og, seeded.normal_fields(101, og.shape))
+    t0 = time.time()
+    for _ in range(reps):
+        out = P.full(D.jvp_full(og, GR, q, v))
+    dt = (time.time() - t0) / reps
+    del out
+    return dt
+
+
+def cpu_baseline(n):
+    """The oracle timed on this host: one full n^3 J.v + projection in a single-threaded subprocess."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-only", "--grid", str(n)],
+                           env=env, capture_output=True, text=True, timeout=900)
+        sec = float(json.loads(r.stdout.strip().splitlines()[-1])["seconds"])
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)[:200]}
+    return {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full {n}^3 J.v + projection (FP64 numpy oracle, fast-diagonalisation solve), "
+                      f"{sec:.1f} s, single thread (BLAS threads = 1)", "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def reference_arm(args, ws, rank):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, same workload and metric."""
+    if rank != 0:
+        return None
+    n = args.grid
+    W, K = max(1, min(args.warmup, 1)), args.steps
+    oracle_step_seconds(n, W)
+    t0 = time.time()
+    for _ in range(K):
+        oracle_step_seconds(n, 1)
+    sec = (time.time() - t0) / K
+    value = 1.0 / sec
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    cb = {"value": round(value, 5), "unit": UNIT, "cores": int(threads) if threads.isdigit() else os.cpu_count(),
+          "kind": "oracle", "sample": f"{K} full {n}^3 J.v + projections (FP64 numpy oracle)", "cpu": cpu_model()}
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{n}^3 tanh-stretched (s=1.5) cube, Gr=2e8, Pr=0.71: J.v + projection",
+                       "grid": [n, n, n]},
+            "cpu_baseline": cb, "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.cpu_sample_only:
+        print(json.dumps({"seconds": oracle_step_seconds(args.grid, 1)}))
+        return
+    ws, rank, local = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+                       int(os.environ.get("LOCAL_RANK", "0")))
+    if args.impl == "reference":
+        res = reference_arm(args, ws, rank)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    ws, rank, local = dist_setup(args.gpus)
+    res = gpu_arm(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * cube_fv.h -- C-ABI of the GB300 (sm_103a) library for the Newton-Krylov and
+ * Chebyshev-preconditioned Arnoldi stability analysis of air convection in a
+ * laterally heated cube (Gelfgat, "Sequence of bifurcations of natural
+ * convection of air in a laterally heated cube with perfectly insulated
+ * horizontal and spanwise boundaries").
+ *
+ * Problem (Section 2, Eqs. 1-6), written with unit viscosity ("Form A"):
+ *     dv/dt = -div(v v) + Lap v + Gr T e_z - grad p,   dT/dt = -div(v T) + Lap T / Pr,   div v = 0
+ * in the cube [0,1]^3, no-slip walls, T = 1 at x = 0 and T = 0 at x = 1
+ * (Eq. 4), dT/dy = 0 at y = 0, 1 (Eq. 5), dT/dz = 0 at z = 0, 1 (Eq. 6).
+ * The paper's rescaled form (Section 2) has eigenvalues lambda_B with
+ * lambda_A = Gr^(1/2) lambda_B.
+ *
+ * Discretisation: staggered (MAC) finite volumes on a tensor grid, conservative
+ * central fluxes with linear interpolation, half-cell wall distances.
+ *
+ * ---------------------------------------------------------------- layout
+ * A "state" or "vector" is ONE contiguous device buffer of 4 * nz*ny*nx
+ * elements holding four blocks [u | v | w | T].  Each block is an (nz, ny, nx)
+ * array, x fastest: element (k, j, i) is at (k*ny + j)*nx + i.
+ *     u[k][j][i]: x-velocity on the x-face x_f[i] of cell row (j, k); slot i = 0
+ *                 is the wall x = 0; the wall x = 1 is not stored;
+ *     v[k][j][i]: y-velocity on the y-face y_f[j]; slot j = 0 is the wall y = 0;
+ *     w[k][j][i]: z-velocity on the z-face z_f[k]; slot k = 0 is the wall z = 0;
+ *     T[k][j][i]: temperature at the cell centre.
+ * Wall slots are written as 0 by every entry point and ignored on input; a
+ * caller that runs its own inner products must keep them 0.
+ * Element type: double for FV_FP64, float for FV_FP32 (per call).
+ *
+ * ---------------------------------------------------------------- conventions
+ * All vector arguments are DEVICE pointers owned by the caller, unless a
+ * comment says "host".  The library never frees or reallocates caller memory;
+ * its workspace belongs to the fv_grid handle.  Every call is ordered on the
+ * handle's CUDA stream; entry points that return host scalars synchronise that
+ * stream.  Every entry point returns a status (FV_OK = 0 or a negative
+ * FV_E* code); nothing is thrown across the ABI.  fv_last_error() gives a
+ * message for the last failure on the calling thread.
+ */
+#ifndef CUBE_FV_H
+#define CUBE_FV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FV_OK = 0,
+    FV_EINVAL = -1,    /* bad argument (size, pointer, precision, option) */
+    FV_ENOMEM = -2,    /* device or host allocation failed */
+    FV_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    FV_ENOCONV = -4,   /* iteration limit reached; outputs hold the last iterate */
+    FV_ENAN = -5,      /* NaN or Inf met in a reduction */
+    FV_ETIMEOUT = -6   /* a bounded device-side wait gave up */
+};
+
+enum { FV_FP64 = 0, FV_FP32 = 1 };
+
+typedef struct fv_grid_s* fv_grid;
+
+/* Grid description.  Faces per axis: if xf/yf/zf are NULL the library builds
+ * them: stretch == 0 gives the uniform grid i/n, otherwise the tanh law
+ * x_f[i] = (1 + tanh(s (2i/n - 1)) / tanh(s)) / 2 mirrored about 1/2
+ * (Section 4.1 only says "stretched near the borders"; the law is this
+ * library's reading).  Given arrays are host, n+1 strictly increasing values
+ * with x_f[0] = 0 and x_f[n] = 1.  2 <= n <= 1024 per axis. */
+typedef struct {
+    int nx, ny, nz;
+    const double *xf, *yf, *zf;
+    double stretch;
+    double Pr;          /* Prandtl number (0.71 for air, Section 1) */
+} fv_grid_desc;
+
+/* Create a grid handle: metric arrays, the 1D generalised eigen-decompositions
+ * used by the pressure solve (computed on the host in FP64), and workspace.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: FV_EINVAL (sizes, faces), FV_ENOMEM, FV_ECUDA. */
+int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out);
+int fv_grid_destroy(fv_grid g);
+int fv_set_stream(fv_grid g, void* stream);
+/* Number of elements of one state/vector buffer: 4*nx*ny*nz. */
+long long fv_state_elems(fv_grid g);
+
+/* Residual F(q; Gr) of Eqs. 1-2 without the pressure gradient (Section 2),
+ * FP64 always: F_u = -div(u u) + Lap u, F_w additionally + Gr T_face,
+ * F_T = -div(u T) + Lap T / Pr with the Dirichlet data of Eq. 4.
+ * q, F: device double[4*N].  F is not projected.  Errors: FV_EINVAL, FV_ECUDA. */
+int fv_residual(fv_grid g, double Gr, const double* q, double* F);
+
+/* Jacobian-vector product J(q) v, the exact derivative of F (F is quadratic):
+ * J v = -div(q v) - div(v q) + Lap v + Gr T_v e_z, thermal Dirichlet data 0.
+ * prec selects the element type of q, v and Jv.  Errors: FV_EINVAL, FV_ECUDA. */
+int fv_jvp(fv_grid g, int prec, double Gr, const void* q, const void* v, void* Jv);
+
+/* SIMPLE-like projection (Section 1 methods paragraph, Section 3): replaces the
+ * velocity part of v by P v = v - G phi with DG phi = D v (cell-centred Neumann
+ * problem, solved directly by fast diagonalisation), so that D P v = 0; T is
+ * unchanged.  In place.  max_it >= 1 is the number of solves (each later one
+ * corrects the divergence left by the previous); stops early when
+ * ||D P v||_2 <= tol * ||D v||_2.  iters (host, may be NULL) gets the solves
+ * done; div_rel (host, may be NULL) gets ||D P v||_2 / ||D v||_2 (computing it
+ * costs one more pass).  Errors: FV_EINVAL, FV_ECUDA. */
+int fv_project(fv_grid g, int prec, void* v, int max_it, double tol, int* iters, double* div_rel);
+
+/* Fused hot path: out = P (J(q) v - sigma v) + sigma v.  With sigma = 0 this
+ * is P J(q) v, one "J.v + projection".  For D v = 0 the result does not
+ * depend on sigma; sigma < 0 moves the gradient complement, on which P J
+ * vanishes, to the eigenvalue sigma (used by the Krylov drivers).
+ * out must not alias q or v.  Errors: FV_EINVAL, FV_ECUDA. */
+int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma,
+                   const void* q, const void* v, void* out);
+
+/* Fused recurrence step (the Chebyshev filter's three-term recurrence, Section 1 ref. 21):
+ *     out = alpha (P (J(q) v - sigma v) + sigma v) + beta v + gamma w
+ * with the axpys folded into the projection's correction pass.  w may be NULL
+ * (gamma ignored) and out may alias w, not q or v.  Errors: FV_EINVAL, FV_ECUDA. */
+int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
+                           const void* w, double alpha, double beta, double gamma, void* out);
+
+/* Krylov inner product <a, b> over all 4N elements, accumulated in FP64 in a
+ * fixed order (bit-reproducible).  result: host.  Errors: FV_EINVAL, FV_ECUDA, FV_ENAN. */
+int fv_dot(fv_grid g, int prec, const void* a, const void* b, double* result);
+/* y <- alpha x + beta y over 4N elements (coefficients applied in FP64). */
+int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y);
+/* Element-type conversion of a state: FP64 -> FP32 (to_fp32 = 1) or back. */
+int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst);
+
+/* ---------------------------------------------------------------- Newton */
+typedef struct {
+    int precision;        /* FV_FP64: everything FP64.  FV_FP32: Krylov vectors and
+                             J.v+projection in FP32; residual, updates and inner
+                             products FP64 (the outer loop refines to FP64). */
+    double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) */
+    double krylov_tol;    /* relative residual of each inner solve */
+    int max_newton;       /* Newton steps */
+    int max_matvec;       /* J.v+projections per inner solve */
+    int gmres_m;          /* restart length of the GMRES fallback */
+    double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr */
+    double gr_ratio;      /* continuation factor per step (> 1) */
+} fv_newton_opts;
+
+typedef struct {
+    int status;           /* FV_OK or FV_ENOCONV */
+    int newton_steps;     /* at the final Gr */
+    int matvecs;          /* J.v+projections, all continuation steps */
+    int gmres_fallbacks;  /* inner solves finished by GMRES */
+    int continuation_steps;
+    double residual0;     /* ||P F(q)||_inf at the start of the final Gr */
+    double residual;      /* ||P F(q)||_inf at the end (FP64) */
+    double history[64];   /* ||P F||_inf per Newton step at the final Gr */
+} fv_newton_report;
+
+void fv_newton_default_opts(fv_newton_opts* o);
+
+/* Steady state by Newton's method (Section 1 methods paragraph): solve
+ * P F(q) = 0 for divergence-free q; corrections from (P J(q)) delta = -P F(q)
+ * by BiCGstab(2) (Sleijpen & Fokkema), with GMRES(m) taking over from the
+ * current iterate on breakdown or stagnation.  q_inout: device double[4N],
+ * the initial state (its velocity must be divergence free, e.g. conduction
+ * u = 0, T = 1 - x) and on return the last iterate.  Returns FV_OK,
+ * FV_ENOCONV (report filled, q holds the last iterate), FV_ENAN, FV_EINVAL,
+ * FV_ECUDA, FV_ENOMEM. */
+int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_newton_opts* opts,
+                  fv_newton_report* report);
+
+/* ---------------------------------------------------------------- Arnoldi */
+typedef struct {
+    int precision;        /* FV_FP64, or FV_FP32 Krylov vectors with FP64 Hessenberg,
+                             Gram-Schmidt coefficients and inner products */
+    int m;                /* Krylov subspace dimension per cycle */
+    double tol;           /* stop when every wanted Ritz pair has
+                             ||A x - lam x|| <= tol |lam| (Arnoldi estimate) */
+    int max_restarts;
+    int max_degree;       /* Chebyshev filter degree cap per restart */
+    int min_degree;
+    int guard;            /* extra Ritz values kept outside the filter's ellipse */
+    unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected */
+    double sigma;         /* shift of the gradient complement; 0 = automatic */
+} fv_arnoldi_opts;
+
+typedef struct {
+    int status;           /* FV_OK or FV_ENOCONV */
+    int nconv;            /* number of values returned (k, or k+1 to complete a pair) */
+    int restarts;
+    long long matvecs;
+    double residual[64];  /* ||A x - lam x|| / |lam| per returned value (FP64 recomputation) */
+    double lam_scaled_re[64], lam_scaled_im[64];   /* lam / sqrt(Gr): the paper's scaling */
+    int degrees[256];     /* Chebyshev degree per restart */
+    double seconds;
+} fv_arnoldi_report;
+
+void fv_arnoldi_default_opts(fv_arnoldi_opts* o);
+
+/* Leading eigenvalues (largest real part) of the linearised problem about
+ * the steady state q: lam v = J(q) v - G p, D v = 0, i.e. of P J(q) on the
+ * divergence-free subspace, by Chebyshev-preconditioned Arnoldi (Section 1
+ * methods paragraph and its ref. 21; Section 4.1 uses four).  q: device
+ * double[4N].  re, im: host double[k+1] (a conjugate pair straddling the cut
+ * is completed, so up to k+1 values; report->nconv says how many), ordered by
+ * real part descending, then +Im first.  vecs: NULL or a device buffer of
+ * (k+1)*4N elements of the chosen precision; a complex pair occupies two
+ * consecutive slots (Re, Im).  Form A units; report carries lam/sqrt(Gr).
+ * Errors: FV_EINVAL (k < 1, k+guard+2 > m, m > 200), FV_ENOCONV, FV_ENAN,
+ * FV_ECUDA, FV_ENOMEM. */
+int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, const fv_arnoldi_opts* opts,
+                    double* re, double* im, void* vecs, fv_arnoldi_report* report);
+
+/* ---------------------------------------------------------------- measurement */
+/* Per-kernel-class timing with CUDA events recorded on the handle's stream around every launch.
+ * fv_profile(g, 1) clears and starts recording, fv_profile(g, 0) stops.  fv_profile_read
+ * synchronises the stream and returns, per class (host arrays of FV_PROF_CLASSES), the summed
+ * milliseconds and the launch counts.  Classes: 0 stencil (F, J.v), 1 divergence, 2 pressure-solve
+ * transforms, 3 gradient correction, 4 reductions, 5 other vector kernels.
+ * Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
+enum { FV_PROF_CLASSES = 6 };
+int fv_profile(fv_grid g, int enable);
+int fv_profile_read(fv_grid g, double* ms, long long* launches);
+
+const char* fv_strerror(int status);
+const char* fv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUBE_FV_H */

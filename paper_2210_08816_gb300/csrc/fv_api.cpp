@@ -1,0 +1,1140 @@
+// The C-ABI (include/cube_fv.h): grid set-up, the J.v + projection hot path, and the host drivers of
+// Newton's method (BiCGstab(2) + GMRES) and the Chebyshev-preconditioned Arnoldi iteration (Section 1,
+// methods paragraph).  Every vector operation runs in the library's CUDA kernels; the host holds only
+// scalars and the small dense matrices (Hessenberg, 2 x 2 minimal-residual systems).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <type_traits>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fv_internal.h"
+
+namespace fv {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int cuda_status(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return FV_ECUDA;
+}
+static int invalid(const std::string& msg) {
+  set_error(msg);
+  return FV_EINVAL;
+}
+
+// ------------------------------------------------------------------ measurement
+static cudaEvent_t pool_event(const fv_grid_s* g) {
+  Profiler& p = g->prof;
+  if (p.used == p.pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p.pool.push_back(e);
+  }
+  return p.pool[p.used++];
+}
+
+ProfScope::ProfScope(const fv_grid_s* grid, int kind) : g(grid) {
+  if (!g->prof.enabled) return;
+  cudaEvent_t a = pool_event(g), b = pool_event(g);
+  if (!a || !b) return;
+  cudaEventRecord(a, g->stream);
+  stop = b;
+  g->prof.records.push_back({kind, a, b});
+}
+
+ProfScope::~ProfScope() {
+  if (stop) cudaEventRecord(stop, g->stream);
+}
+
+// ------------------------------------------------------------------ device memory helper
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = count;
+    if (count == 0) return FV_OK;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return FV_ENOMEM;
+    }
+    return FV_OK;
+  }
+};
+
+// ------------------------------------------------------------------ grid construction
+static std::vector<double> tanh_faces(int n, double s) {
+  std::vector<double> f(n + 1);
+  for (int i = 0; i <= n; ++i)
+    f[i] = (s == 0.0) ? (double)i / n : 0.5 * (1.0 + std::tanh(s * (2.0 * i / n - 1.0)) / std::tanh(s));
+  for (int k = 0; k <= n / 2; ++k) f[n - k] = 1.0 - f[k];
+  if (n % 2 == 0) f[n / 2] = 0.5;
+  f[0] = 0.0;
+  f[n] = 1.0;
+  return f;
+}
+
+struct AxisHost {
+  int n;
+  std::vector<double> idx, idc, wl, wr, lam, Einv, E;
+};
+
+static int build_axis(const std::vector<double>& xf, AxisHost& a) {
+  const int n = (int)xf.size() - 1;
+  a.n = n;
+  std::vector<double> dx(n), xc(n);
+  for (int i = 0; i < n; ++i) {
+    dx[i] = xf[i + 1] - xf[i];
+    xc[i] = 0.5 * (xf[i] + xf[i + 1]);
+    if (!(dx[i] > 0.0)) return invalid("faces must be strictly increasing");
+  }
+  a.idx.assign(n + 1, 0.0);
+  a.idc.assign(n + 1, 0.0);
+  a.wl.assign(n + 1, 0.0);
+  a.wr.assign(n + 1, 0.0);
+  for (int i = 0; i < n; ++i) a.idx[i] = 1.0 / dx[i];
+  a.idc[0] = 2.0 / dx[0];
+  a.idc[n] = 2.0 / dx[n - 1];
+  for (int f = 1; f < n; ++f) {
+    a.idc[f] = 1.0 / (xc[f] - xc[f - 1]);
+    a.wl[f] = dx[f] / (dx[f - 1] + dx[f]);
+    a.wr[f] = dx[f - 1] / (dx[f - 1] + dx[f]);
+  }
+  // 1D Neumann operator A = W^-1 S; symmetric form B = W^-1/2 S W^-1/2 (tridiagonal)
+  std::vector<double> d(n), e(std::max(n - 1, 1), 0.0);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    if (i >= 1) s -= a.idc[i];
+    if (i + 1 <= n - 1) s -= a.idc[i + 1];
+    d[i] = s / dx[i];
+    if (i + 1 <= n - 1) e[i] = a.idc[i + 1] / std::sqrt(dx[i] * dx[i + 1]);
+  }
+  std::vector<double> Q;
+  if (!tridiag_eig(n, d, e, Q)) return invalid("tridiagonal eigensolver did not converge");
+  std::vector<int> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int p, int q) { return d[p] > d[q]; });
+  a.lam.assign(n, 0.0);
+  a.Einv.assign((size_t)n * n, 0.0);
+  a.E.assign((size_t)n * n, 0.0);
+  for (int m = 0; m < n; ++m) {
+    const int src = ord[m];
+    a.lam[m] = (m == 0) ? 0.0 : d[src];  // the constant vector is an exact null vector
+    for (int i = 0; i < n; ++i) {
+      const double qv = Q[(size_t)i * n + src];
+      a.E[(size_t)i * n + m] = qv / std::sqrt(dx[i]);
+      a.Einv[(size_t)m * n + i] = qv * std::sqrt(dx[i]);
+    }
+  }
+  return FV_OK;
+}
+
+template <typename R>
+static int upload_axes(fv_grid_s* g, const AxisHost* ax, int which, Geo<R>& geo, FdmDev<R>& fdm) {
+  size_t total = 0;
+  for (int d = 0; d < 3; ++d) total += 4 * (size_t)(ax[d].n + 1) + ax[d].n + 2 * (size_t)ax[d].n * ax[d].n;
+  std::vector<R> h(total);
+  std::vector<size_t> off;
+  size_t o = 0;
+  auto put = [&](const std::vector<double>& v) {
+    off.push_back(o);
+    for (double x : v) h[o++] = (R)x;
+  };
+  for (int d = 0; d < 3; ++d) {
+    put(ax[d].idx);
+    put(ax[d].idc);
+    put(ax[d].wl);
+    put(ax[d].wr);
+    put(ax[d].lam);
+    put(ax[d].Einv);
+    put(ax[d].E);
+  }
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, total * sizeof(R));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc metrics: ") + cudaGetErrorString(e));
+    return FV_ENOMEM;
+  }
+  g->metric_buf[which] = buf;
+  FV_CUDA(cudaMemcpy(buf, h.data(), total * sizeof(R), cudaMemcpyHostToDevice));
+  const R* base = (const R*)buf;
+  for (int d = 0; d < 3; ++d) {
+    geo.n[d] = ax[d].n;
+    geo.idx[d] = base + off[7 * d + 0];
+    geo.idc[d] = base + off[7 * d + 1];
+    geo.wl[d] = base + off[7 * d + 2];
+    geo.wr[d] = base + off[7 * d + 3];
+    fdm.lam[d] = base + off[7 * d + 4];
+    fdm.Einv[d] = base + off[7 * d + 5];
+    fdm.E[d] = base + off[7 * d + 6];
+  }
+  return FV_OK;
+}
+
+template <typename R>
+static constexpr int prec_index() {
+  return sizeof(R) == 8 ? 0 : 1;
+}
+
+template <typename R>
+static int ensure_ws(fv_grid_s* g) {
+  const int p = prec_index<R>();
+  if (g->ws.Y[p]) return FV_OK;
+  const size_t N = g->N;
+  void *Y = nullptr, *t0 = nullptr, *t1 = nullptr;
+  if (cudaMalloc(&Y, 4 * N * sizeof(R)) != cudaSuccess || cudaMalloc(&t0, N * sizeof(R)) != cudaSuccess ||
+      cudaMalloc(&t1, N * sizeof(R)) != cudaSuccess) {
+    if (Y) cudaFree(Y);
+    if (t0) cudaFree(t0);
+    cudaGetLastError();
+    set_error("workspace allocation failed");
+    return FV_ENOMEM;
+  }
+  g->ws.Y[p] = Y;
+  g->ws.t0[p] = t0;
+  g->ws.t1[p] = t1;
+  return FV_OK;
+}
+
+// ------------------------------------------------------------------ the hot path
+template <typename R>
+int jvp_project(fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out) {
+  FV_TRY(ensure_ws<R>(g));
+  const int p = prec_index<R>();
+  R* Y = (R*)g->ws.Y[p];
+  R* phi = (R*)g->ws.t1[p];
+  R* tmp = (R*)g->ws.t0[p];
+  FV_TRY(launch_jvp<R>(g, Gr, sigma, q, v, Y));
+  FV_TRY(launch_divergence<R>(g, Y, phi));
+  FV_TRY(launch_poisson<R>(g, phi, phi, tmp));
+  FV_TRY(launch_correct<R>(g, Y, phi, 1.0, sigma != 0.0 ? v : nullptr, sigma, nullptr, 0.0, out));
+  return FV_OK;
+}
+
+// out = alpha (P(J y - sigma y)) + beta y + gamma yprev   (one step of a three-term recurrence in A)
+template <typename R>
+int chebyshev_step(fv_grid_s* g, double Gr, double sigma, const R* q, const R* y, const R* yprev, double alpha,
+                   double beta, double gamma, R* out) {
+  FV_TRY(ensure_ws<R>(g));
+  const int p = prec_index<R>();
+  R* Y = (R*)g->ws.Y[p];
+  R* phi = (R*)g->ws.t1[p];
+  R* tmp = (R*)g->ws.t0[p];
+  FV_TRY(launch_jvp<R>(g, Gr, sigma, q, y, Y));
+  FV_TRY(launch_divergence<R>(g, Y, phi));
+  FV_TRY(launch_poisson<R>(g, phi, phi, tmp));
+  FV_TRY(launch_correct<R>(g, Y, phi, alpha, y, beta, yprev, gamma, out));
+  return FV_OK;
+}
+
+template <typename R>
+static int project_inplace(fv_grid_s* g, R* v, int max_it, double tol, int* iters, double* div_rel) {
+  FV_TRY(ensure_ws<R>(g));
+  const int p = prec_index<R>();
+  R* phi = (R*)g->ws.t1[p];
+  R* tmp = (R*)g->ws.t0[p];
+  const bool want = (div_rel != nullptr) || max_it > 1;
+  double d0 = 0.0, dn = 0.0;
+  int it = 0;
+  FV_TRY(launch_divergence<R>(g, v, phi));
+  if (want) {
+    FV_TRY(launch_dot<R>(g, phi, phi, g->N, 0));
+    FV_TRY(read_scalars(g, 0, 1, &d0));
+    d0 = std::sqrt(d0);
+  }
+  for (it = 1; it <= std::max(1, max_it); ++it) {
+    FV_TRY(launch_poisson<R>(g, phi, phi, tmp));
+    FV_TRY(launch_correct<R>(g, v, phi, 1.0, nullptr, 0.0, nullptr, 0.0, v));
+    if (!want) break;
+    FV_TRY(launch_divergence<R>(g, v, phi));
+    FV_TRY(launch_dot<R>(g, phi, phi, g->N, 0));
+    FV_TRY(read_scalars(g, 0, 1, &dn));
+    dn = std::sqrt(dn);
+    if (!(dn > tol * d0) || it == max_it) break;
+  }
+  if (iters) *iters = std::min(it, std::max(1, max_it));
+  if (div_rel) *div_rel = (d0 > 0.0) ? dn / d0 : 0.0;
+  return FV_OK;
+}
+
+// ------------------------------------------------------------------ small vector toolkit over device vectors
+template <typename R>
+struct Vec {
+  fv_grid_s* g;
+  size_t n;
+  int dot(const R* a, const R* b, double* out) {
+    FV_TRY(launch_dot<R>(g, a, b, n, 0));
+    FV_TRY(read_scalars(g, 0, 1, out));
+    if (!std::isfinite(*out)) {
+      set_error("non-finite inner product");
+      return FV_ENAN;
+    }
+    return FV_OK;
+  }
+  int lin(R* out, std::initializer_list<std::pair<double, const R*>> terms) {
+    double c[4];
+    const R* x[4];
+    int k = 0;
+    for (auto& t : terms) {
+      c[k] = t.first;
+      x[k] = t.second;
+      ++k;
+    }
+    return launch_lincomb<R>(g, n, k, c, x, out);
+  }
+  int copy(R* dst, const R* src) {
+    FV_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(R), cudaMemcpyDeviceToDevice, g->stream));
+    return FV_OK;
+  }
+  int zero(R* dst) {
+    FV_CUDA(cudaMemsetAsync(dst, 0, n * sizeof(R), g->stream));
+    return FV_OK;
+  }
+};
+
+// ------------------------------------------------------------------ BiCGstab(2) and GMRES
+template <typename R>
+struct Operator {
+  fv_grid_s* g;
+  double Gr, sigma;
+  const R* q;
+  long long* matvecs;
+  int apply(const R* x, R* y) {
+    ++*matvecs;
+    return jvp_project<R>(g, Gr, sigma, q, x, y);
+  }
+};
+
+struct SolveInfo {
+  int status = FV_ENOCONV;  // FV_OK converged
+  bool breakdown = false, stalled = false;
+  int matvecs = 0;
+  double rel = 1.0;
+};
+
+// BiCGstab(l), l = 2 (Sleijpen & Fokkema 1993): two BiCG steps, then the minimal-residual polynomial
+// update min || r0 - g1 r1 - g2 r2 || by its 2 x 2 normal equations.
+template <typename R>
+static int bicgstab2(Operator<R>& A, const R* b, R* x, double tol, int max_mv, R* work, SolveInfo& info) {
+  Vec<R> V{A.g, 4 * A.g->N};
+  const size_t n = V.n;
+  R *r = work, *rt = work + n, *u = work + 2 * n, *u1 = work + 3 * n, *u2 = work + 4 * n, *r1 = work + 5 * n,
+    *r2 = work + 6 * n;
+  FV_TRY(V.zero(x));
+  FV_TRY(V.copy(r, b));
+  FV_TRY(V.copy(rt, b));
+  FV_TRY(V.zero(u));
+  double bn2;
+  FV_TRY(V.dot(b, b, &bn2));
+  const double bn = std::sqrt(bn2);
+  info = SolveInfo{};
+  if (bn == 0.0) {
+    info.status = FV_OK;
+    info.rel = 0.0;
+    return FV_OK;
+  }
+  double rho0 = 1.0, alpha = 0.0, omega = 1.0, best = 1.0;
+  int best_cycle = 0, cycle = 0;
+  const long long mv0 = *A.matvecs;
+  for (;;) {
+    info.matvecs = (int)(*A.matvecs - mv0);
+    if (info.rel <= tol) {
+      info.status = FV_OK;
+      return FV_OK;
+    }
+    if (info.matvecs + 4 > max_mv) return FV_OK;
+    rho0 = -omega * rho0;
+    double rho1, gamma;
+    // j = 0
+    FV_TRY(V.dot(r, rt, &rho1));
+    if (rho0 == 0.0 || rho1 == 0.0) {
+      info.breakdown = true;
+      return FV_OK;
+    }
+    double beta = alpha * rho1 / rho0;
+    rho0 = rho1;
+    FV_TRY(V.lin(u, {{1.0, r}, {-beta, u}}));
+    FV_TRY(A.apply(u, u1));
+    FV_TRY(V.dot(u1, rt, &gamma));
+    if (gamma == 0.0) {
+      info.breakdown = true;
+      return FV_OK;
+    }
+    alpha = rho0 / gamma;
+    FV_TRY(V.lin(r, {{1.0, r}, {-alpha, u1}}));
+    FV_TRY(A.apply(r, r1));
+    FV_TRY(V.lin(x, {{1.0, x}, {alpha, u}}));
+    // j = 1
+    FV_TRY(V.dot(r1, rt, &rho1));
+    if (rho1 == 0.0) {
+      info.breakdown = true;
+      return FV_OK;
+    }
+    beta = alpha * rho1 / rho0;
+    rho0 = rho1;
+    FV_TRY(V.lin(u, {{1.0, r}, {-beta, u}}));
+    FV_TRY(V.lin(u1, {{1.0, r1}, {-beta, u1}}));
+    FV_TRY(A.apply(u1, u2));
+    FV_TRY(V.dot(u2, rt, &gamma));
+    if (gamma == 0.0) {
+      info.breakdown = true;
+      return FV_OK;
+    }
+    alpha = rho0 / gamma;
+    FV_TRY(V.lin(r, {{1.0, r}, {-alpha, u1}}));
+    FV_TRY(V.lin(r1, {{1.0, r1}, {-alpha, u2}}));
+    FV_TRY(A.apply(r1, r2));
+    FV_TRY(V.lin(x, {{1.0, x}, {alpha, u}}));
+    // minimal residual part
+    double g11, g12, g22, c1, c2;
+    FV_TRY(V.dot(r1, r1, &g11));
+    FV_TRY(V.dot(r1, r2, &g12));
+    FV_TRY(V.dot(r2, r2, &g22));
+    FV_TRY(V.dot(r1, r, &c1));
+    FV_TRY(V.dot(r2, r, &c2));
+    std::vector<double> G = {g11, g12, g12, g22}, c = {c1, c2};
+    if (!dense_solve(2, G, c)) {
+      info.breakdown = true;
+      return FV_OK;
+    }
+    FV_TRY(V.lin(x, {{1.0, x}, {c[0], r}, {c[1], r1}}));
+    FV_TRY(V.lin(r, {{1.0, r}, {-c[0], r1}, {-c[1], r2}}));
+    FV_TRY(V.lin(u, {{1.0, u}, {-c[0], u1}, {-c[1], u2}}));
+    omega = c[1];
+    double rr;
+    FV_TRY(V.dot(r, r, &rr));
+    info.rel = std::sqrt(rr) / bn;
+    ++cycle;
+    if (info.rel <= 0.5 * best) {
+      best = info.rel;
+      best_cycle = cycle;
+    } else if (cycle - best_cycle >= 20) {
+      info.stalled = true;
+      info.matvecs = (int)(*A.matvecs - mv0);
+      return FV_OK;
+    }
+  }
+}
+
+// Restarted GMRES(m) from the initial guess in x, classical Gram-Schmidt applied twice.
+template <typename R>
+static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv, R* basis, R* w, SolveInfo& info) {
+  Vec<R> V{A.g, 4 * A.g->N};
+  const size_t n = V.n;
+  fv_grid_s* g = A.g;
+  double bn2;
+  FV_TRY(V.dot(b, b, &bn2));
+  const double bn = std::sqrt(bn2);
+  const long long mv0 = *A.matvecs;
+  info = SolveInfo{};
+  if (bn == 0.0) {
+    info.status = FV_OK;
+    info.rel = 0.0;
+    return FV_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), h(m + 1), h2(m + 1), y;
+  for (;;) {
+    // r = b - A x into basis[0]
+    FV_TRY(A.apply(x, w));
+    FV_TRY(V.lin(basis, {{1.0, b}, {-1.0, w}}));
+    double beta2;
+    FV_TRY(V.dot(basis, basis, &beta2));
+    const double beta = std::sqrt(beta2);
+    info.rel = beta / bn;
+    info.matvecs = (int)(*A.matvecs - mv0);
+    if (info.rel <= tol) {
+      info.status = FV_OK;
+      return FV_OK;
+    }
+    if (info.matvecs >= max_mv) return FV_OK;
+    FV_TRY(V.lin(basis, {{1.0 / beta, basis}}));
+    std::fill(H.begin(), H.end(), 0.0);
+    int used = 0;
+    for (int j = 0; j < m; ++j) {
+      FV_TRY(A.apply(basis + (size_t)j * n, w));
+      for (int pass = 0; pass < 2; ++pass) {
+        FV_TRY(launch_multidot<R>(g, basis, n, j + 1, w, n, 1));
+        FV_TRY(launch_subtract_basis<R>(g, basis, n, j + 1, g->ws.scalars + 1, w, n));
+        FV_TRY(read_scalars(g, 1, j + 1, h.data()));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+      }
+      double wn2;
+      FV_TRY(V.dot(w, w, &wn2));
+      H[(size_t)(j + 1) * m + j] = std::sqrt(wn2);
+      used = j + 1;
+      double res;
+      hessenberg_lstsq(used, H.data(), m, beta, y, &res);
+      const bool done = res <= tol * bn || *A.matvecs - mv0 >= max_mv || wn2 == 0.0;
+      if (!done) FV_TRY(V.lin(basis + (size_t)(j + 1) * n, {{1.0 / std::sqrt(wn2), w}}));
+      if (done) break;
+    }
+    hessenberg_lstsq(used, H.data(), m, beta, y, nullptr);
+    for (int i = 0; i < used; ++i) h2[i] = -y[i];
+    FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, h2.data(), sizeof(double) * used, cudaMemcpyHostToDevice, g->stream));
+    FV_TRY(launch_subtract_basis<R>(g, basis, n, used, g->ws.scalars + 1, x, n));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+  }
+}
+
+}  // namespace fv
+
+using namespace fv;
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* fv_strerror(int s) {
+  switch (s) {
+    case FV_OK: return "ok";
+    case FV_EINVAL: return "invalid argument";
+    case FV_ENOMEM: return "out of memory";
+    case FV_ECUDA: return "CUDA error";
+    case FV_ENOCONV: return "iteration did not converge";
+    case FV_ENAN: return "NaN or Inf in a reduction";
+    case FV_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* fv_last_error(void) { return g_last_error.c_str(); }
+
+int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out) {
+  if (!desc || !out) return invalid("null argument");
+  *out = nullptr;
+  const int n[3] = {desc->nx, desc->ny, desc->nz};
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 2 || n[d] > kMaxN) return invalid("grid size out of range [2, 1024]");
+  if (!(desc->Pr > 0.0)) return invalid("Pr must be positive");
+  const double* given[3] = {desc->xf, desc->yf, desc->zf};
+  fv_grid_s* g = new fv_grid_s();
+  g->nx = n[0];
+  g->ny = n[1];
+  g->nz = n[2];
+  g->N = (size_t)n[0] * n[1] * n[2];
+  g->Pr = desc->Pr;
+  g->stream = (cudaStream_t)stream;
+  AxisHost ax[3];
+  int st = FV_OK;
+  for (int d = 0; d < 3 && st == FV_OK; ++d) {
+    if (given[d]) {
+      g->xf[d].assign(given[d], given[d] + n[d] + 1);
+      if (g->xf[d][0] != 0.0 || g->xf[d][n[d]] != 1.0) st = invalid("faces must start at 0 and end at 1");
+    } else {
+      g->xf[d] = tanh_faces(n[d], desc->stretch);
+    }
+    if (st == FV_OK) st = build_axis(g->xf[d], ax[d]);
+    if (st == FV_OK) {
+      double mw = 1.0;
+      for (int i = 0; i < n[d]; ++i) mw = std::min(mw, g->xf[d][i + 1] - g->xf[d][i]);
+      g->min_width[d] = mw;
+    }
+  }
+  if (st == FV_OK) st = upload_axes<double>(g, ax, 0, g->geo64, g->fdm64);
+  if (st == FV_OK) st = upload_axes<float>(g, ax, 1, g->geo32, g->fdm32);
+  if (st == FV_OK) {
+    if (cudaMalloc(&g->ws.partials, sizeof(double) * kReduceBlocks * 256) != cudaSuccess ||
+        cudaMalloc(&g->ws.scalars, sizeof(double) * kMaxScalars) != cudaSuccess ||
+        cudaMallocHost(&g->ws.host_scalars, sizeof(double) * kMaxScalars) != cudaSuccess) {
+      cudaGetLastError();
+      st = FV_ENOMEM;
+      set_error("workspace allocation failed");
+    }
+  }
+  if (st != FV_OK) {
+    fv_grid_destroy(g);
+    return st;
+  }
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) s += 4.0 / (g->min_width[d] * g->min_width[d]);
+  g->sigma_default = -0.5 * std::max(1.0, 1.0 / g->Pr) * s;
+  *out = g;
+  return FV_OK;
+}
+
+int fv_grid_destroy(fv_grid g) {
+  if (!g) return FV_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (g->metric_buf[p]) cudaFree(g->metric_buf[p]);
+    if (g->ws.Y[p]) cudaFree(g->ws.Y[p]);
+    if (g->ws.t0[p]) cudaFree(g->ws.t0[p]);
+    if (g->ws.t1[p]) cudaFree(g->ws.t1[p]);
+  }
+  if (g->ws.partials) cudaFree(g->ws.partials);
+  if (g->ws.scalars) cudaFree(g->ws.scalars);
+  if (g->ws.host_scalars) cudaFreeHost(g->ws.host_scalars);
+  for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  delete g;
+  return FV_OK;
+}
+
+int fv_set_stream(fv_grid g, void* stream) {
+  if (!g) return invalid("null grid");
+  g->stream = (cudaStream_t)stream;
+  return FV_OK;
+}
+
+long long fv_state_elems(fv_grid g) { return g ? (long long)(4 * g->N) : -1; }
+
+int fv_profile(fv_grid g, int enable) {
+  if (!g) return invalid("null grid");
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  if (enable) {
+    g->prof.records.clear();
+    g->prof.used = 0;
+  }
+  g->prof.enabled = enable != 0;
+  return FV_OK;
+}
+
+int fv_profile_read(fv_grid g, double* ms, long long* launches) {
+  if (!g || !ms || !launches) return invalid("null argument");
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  for (int k = 0; k < FV_PROF_CLASSES; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto& r : g->prof.records) {
+    float t = 0.0f;
+    FV_CUDA(cudaEventElapsedTime(&t, r.start, r.stop));
+    if (r.kind >= 0 && r.kind < FV_PROF_CLASSES) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+    }
+  }
+  return FV_OK;
+}
+
+int fv_residual(fv_grid g, double Gr, const double* q, double* F) {
+  if (!g || !q || !F) return invalid("null argument");
+  return launch_residual<double>(g, Gr, q, F);
+}
+
+int fv_jvp(fv_grid g, int prec, double Gr, const void* q, const void* v, void* Jv) {
+  if (!g || !q || !v || !Jv) return invalid("null argument");
+  if (prec == FV_FP64) return launch_jvp<double>(g, Gr, 0.0, (const double*)q, (const double*)v, (double*)Jv);
+  if (prec == FV_FP32) return launch_jvp<float>(g, Gr, 0.0, (const float*)q, (const float*)v, (float*)Jv);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_project(fv_grid g, int prec, void* v, int max_it, double tol, int* iters, double* div_rel) {
+  if (!g || !v) return invalid("null argument");
+  if (prec == FV_FP64) return project_inplace<double>(g, (double*)v, max_it, tol, iters, div_rel);
+  if (prec == FV_FP32) return project_inplace<float>(g, (float*)v, max_it, tol, iters, div_rel);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v, void* out) {
+  if (!g || !q || !v || !out) return invalid("null argument");
+  if (out == q || out == v) return invalid("out must not alias q or v");
+  if (prec == FV_FP64) return jvp_project<double>(g, Gr, sigma, (const double*)q, (const double*)v, (double*)out);
+  if (prec == FV_FP32) return jvp_project<float>(g, Gr, sigma, (const float*)q, (const float*)v, (float*)out);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
+                           const void* w, double alpha, double beta, double gamma, void* out) {
+  if (!g || !q || !v || !out) return invalid("null argument");
+  if (out == q || out == v) return invalid("out must not alias q or v");
+  // alpha (P(Jv - sigma v) + sigma v) + beta v + gamma w = alpha P(Jv - sigma v) + (alpha sigma + beta) v + gamma w
+  const double b2 = alpha * sigma + beta;
+  if (prec == FV_FP64)
+    return chebyshev_step<double>(g, Gr, sigma, (const double*)q, (const double*)v, w ? (const double*)w : nullptr,
+                                  alpha, b2, w ? gamma : 0.0, (double*)out);
+  if (prec == FV_FP32)
+    return chebyshev_step<float>(g, Gr, sigma, (const float*)q, (const float*)v, w ? (const float*)w : nullptr, alpha,
+                                 b2, w ? gamma : 0.0, (float*)out);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_dot(fv_grid g, int prec, const void* a, const void* b, double* result) {
+  if (!g || !a || !b || !result) return invalid("null argument");
+  if (prec == FV_FP64) return Vec<double>{g, 4 * g->N}.dot((const double*)a, (const double*)b, result);
+  if (prec == FV_FP32) return Vec<float>{g, 4 * g->N}.dot((const float*)a, (const float*)b, result);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y) {
+  if (!g || !x || !y) return invalid("null argument");
+  if (prec == FV_FP64) return Vec<double>{g, 4 * g->N}.lin((double*)y, {{alpha, (const double*)x}, {beta, (const double*)y}});
+  if (prec == FV_FP32) return Vec<float>{g, 4 * g->N}.lin((float*)y, {{alpha, (const float*)x}, {beta, (const float*)y}});
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst) {
+  if (!g || !src || !dst) return invalid("null argument");
+  if (to_fp32) return launch_convert(g, 4 * g->N, (const double*)src, (float*)dst);
+  return launch_convert(g, 4 * g->N, (const float*)src, (double*)dst);
+}
+
+void fv_newton_default_opts(fv_newton_opts* o) {
+  if (!o) return;
+  o->precision = FV_FP64;
+  o->tol = 1e-10;
+  o->krylov_tol = 1e-10;
+  o->max_newton = 20;
+  o->max_matvec = 4000;
+  o->gmres_m = 30;
+  o->gr_start = 0.0;
+  o->gr_ratio = 2.0;
+}
+
+void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
+  if (!o) return;
+  o->precision = FV_FP64;
+  o->m = 20;
+  o->tol = 1e-9;
+  o->max_restarts = 200;
+  o->max_degree = 200;
+  o->min_degree = 10;
+  o->guard = 2;
+  o->seed = 1;
+  o->sigma = 0.0;
+}
+
+}  // extern "C"
+
+// ====================================================================== Newton
+namespace fv {
+
+template <typename R>
+static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o, fv_newton_report* rep,
+                     bool record) {
+  const size_t n = 4 * g->N;
+  Vec<double> V64{g, n};
+  DevBuf<double> r64, d64;
+  DevBuf<R> qR, rhs, x, work, basis, w;
+  FV_TRY(r64.alloc(n));
+  FV_TRY(d64.alloc(n));
+  const bool mixed = !std::is_same<R, double>::value;
+  if (mixed) FV_TRY(qR.alloc(n));
+  FV_TRY(rhs.alloc(mixed ? n : 0));
+  FV_TRY(x.alloc(n));
+  FV_TRY(work.alloc(7 * n));
+  FV_TRY(basis.alloc((size_t)(o.gmres_m + 1) * n));
+  FV_TRY(w.alloc(n));
+  const double sigma = g->sigma_default;
+  const double ktol = mixed ? std::max(o.krylov_tol, 1e-5) : o.krylov_tol;
+  double r0 = -1.0;
+  int steps = 0;
+  for (int it = 0;; ++it) {
+    FV_TRY(launch_residual<double>(g, Gr, q, r64.p));
+    FV_TRY(project_inplace<double>(g, r64.p, 1, 0.0, nullptr, nullptr));
+    double rn;
+    FV_TRY(launch_maxabs<double>(g, r64.p, n, 0));
+    FV_TRY(read_scalars(g, 0, 1, &rn));
+    if (!std::isfinite(rn)) {
+      set_error("non-finite Newton residual");
+      return FV_ENAN;
+    }
+    if (r0 < 0.0) r0 = rn;
+    if (record) {
+      if (it < 64) rep->history[it] = rn;
+      rep->residual0 = r0;
+      rep->residual = rn;
+      rep->newton_steps = steps;
+    }
+    if (rn <= o.tol * std::max(1.0, r0)) return FV_OK;
+    if (steps >= o.max_newton) return FV_ENOCONV;
+    // solve (P J(q)) delta = -P F(q)
+    const R* qop;
+    R* b;
+    if (mixed) {
+      FV_TRY(launch_convert(g, n, q, (float*)qR.p));
+      FV_TRY(launch_convert(g, n, r64.p, (float*)rhs.p));
+      qop = qR.p;
+      b = rhs.p;
+    } else {
+      qop = (const R*)q;
+      b = (R*)r64.p;
+    }
+    Vec<R> VR{g, n};
+    FV_TRY(VR.lin(b, {{-1.0, b}}));
+    long long mv = 0;
+    Operator<R> A{g, Gr, sigma, qop, &mv};
+    SolveInfo info;
+    FV_TRY(bicgstab2<R>(A, b, x.p, ktol, o.max_matvec, work.p, info));
+    if (info.status != FV_OK && (info.breakdown || info.stalled)) {
+      SolveInfo info2;
+      FV_TRY(gmres<R>(A, b, x.p, ktol, o.gmres_m, o.max_matvec - info.matvecs, basis.p, w.p, info2));
+      rep->gmres_fallbacks += 1;
+    }
+    rep->matvecs += (int)mv;
+    // delta -> FP64, re-projected in FP64 so that q stays divergence free to FP64 accuracy
+    if (mixed) {
+      FV_TRY(launch_convert(g, n, (const float*)x.p, d64.p));
+    } else {
+      FV_TRY(V64.copy(d64.p, (const double*)x.p));
+    }
+    FV_TRY(project_inplace<double>(g, d64.p, 1, 0.0, nullptr, nullptr));
+    FV_TRY(V64.lin(q, {{1.0, q}, {1.0, d64.p}}));
+    ++steps;
+  }
+}
+
+}  // namespace fv
+
+extern "C" int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_newton_opts* opts,
+                             fv_newton_report* report) {
+  if (!g || !q_inout) return invalid("null argument");
+  fv_newton_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fv_newton_default_opts(&o);
+  if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
+  if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200) return invalid("bad Newton options");
+  fv_newton_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  std::vector<double> ladder;
+  if (o.gr_start > 0.0 && o.gr_start < Gr) {
+    if (!(o.gr_ratio > 1.0)) return invalid("gr_ratio must exceed 1");
+    for (double x = o.gr_start; x < Gr; x *= o.gr_ratio) ladder.push_back(x);
+  }
+  ladder.push_back(Gr);
+  int st = FV_OK;
+  for (size_t i = 0; i < ladder.size(); ++i) {
+    const bool last = (i + 1 == ladder.size());
+    fv_newton_report tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    fv_newton_report* r = last ? &rep : &tmp;
+    st = (o.precision == FV_FP64) ? newton_at<double>(g, ladder[i], q_inout, o, r, true)
+                                  : newton_at<float>(g, ladder[i], q_inout, o, r, true);
+    if (!last) {
+      rep.matvecs += tmp.matvecs;
+      rep.gmres_fallbacks += tmp.gmres_fallbacks;
+      rep.continuation_steps += 1;
+    }
+    if (st != FV_OK) break;
+  }
+  rep.status = st;
+  if (report) *report = rep;
+  return st;
+}
+
+// ====================================================================== Chebyshev-preconditioned Arnoldi
+namespace fv {
+
+struct Ritz {
+  double re, im;
+};
+
+static bool ritz_before(const Ritz& a, const Ritz& b) {
+  if (a.re != b.re) return a.re > b.re;
+  if (std::fabs(a.im) != std::fabs(b.im)) return std::fabs(a.im) > std::fabs(b.im);
+  return a.im > b.im;
+}
+
+// |w| with w = xi + sqrt(xi^2 - 1), xi = (z - d)/c, the branch with |w| >= 1: the level of z in the
+// family of ellipses with foci d +- c (c^2 real, possibly negative; c^2 = 0 gives circles about d).
+static double ellipse_level(double zr, double zi, double d, double c2) {
+  const std::complex<double> z(zr, zi);
+  if (std::fabs(c2) < 1e-300) return std::abs(z - d);
+  const std::complex<double> c = std::sqrt(std::complex<double>(c2, 0.0));
+  const std::complex<double> xi = (z - d) / c;
+  const std::complex<double> s = std::sqrt(xi * xi - 1.0);
+  return std::max(std::abs(xi + s), std::abs(xi - s));
+}
+
+// Scan real-centred ellipses containing the unwanted Ritz values; keep the one whose slowest wanted
+// damping rate min_w level(w) / max_u level(u) is largest.
+static void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz>& unwanted, double& d_out,
+                         double& c2_out, double& rate_out) {
+  double amin = 1e300, amax = -1e300, bmax = 0.0;
+  for (auto& u : unwanted) {
+    amin = std::min(amin, u.re);
+    amax = std::max(amax, u.re);
+    bmax = std::max(bmax, std::fabs(u.im));
+  }
+  const double span = std::max(amax - amin, 1e-12 * std::max(1.0, std::fabs(amax)));
+  rate_out = -1.0;
+  for (int a = 0; a < 13; ++a) {
+    const double d = amin + (0.2 + 0.05 * a) * span;
+    const double a0 = std::max(amax - d, d - amin);
+    for (int t = 0; t <= 40; ++t) {
+      const double c2 = (-1.0 + 0.05 * t) * std::max(a0 * a0, bmax * bmax);
+      double lu = 0.0, lw = 1e300;
+      for (auto& u : unwanted) lu = std::max(lu, ellipse_level(u.re, u.im, d, c2));
+      for (auto& w : wanted) lw = std::min(lw, ellipse_level(w.re, w.im, d, c2));
+      const double rate = lu > 0.0 ? lw / lu : 1e300;
+      if (rate > rate_out) {
+        rate_out = rate;
+        d_out = d;
+        c2_out = c2;
+      }
+    }
+  }
+}
+
+template <typename R>
+static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
+                        double* im, void* vecs_out, fv_arnoldi_report* rep) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t n = 4 * g->N;
+  const int m = o.m;
+  const bool mixed = !std::is_same<R, double>::value;
+  const double sigma = (o.sigma != 0.0) ? o.sigma : g->sigma_default;
+  DevBuf<R> qR, Vb, w, y0, y1;
+  if (mixed) {
+    FV_TRY(qR.alloc(n));
+    FV_TRY(launch_convert(g, n, q64, (float*)qR.p));
+  }
+  const R* q = mixed ? qR.p : (const R*)q64;
+  FV_TRY(Vb.alloc((size_t)(m + 1) * n));
+  FV_TRY(w.alloc(n));
+  FV_TRY(y0.alloc(n));
+  FV_TRY(y1.alloc(n));
+  Vec<R> V{g, n};
+  long long mv = 0;
+  Operator<R> A{g, Gr, sigma, q, &mv};
+  // start vector: seeded N(0,1), projected, normalised
+  R* x = y0.p;
+  FV_TRY(launch_fill_normal<R>(g, o.seed, x));
+  FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
+  std::vector<double> H((size_t)(m + 1) * m), h(m + 1), hre, him, ycoef;
+  std::vector<std::vector<double>> Y;
+  std::vector<Ritz> ritz;
+  std::vector<int> order;
+  int status = FV_ENOCONV, nret = 0;
+  for (int restart = 0; restart <= o.max_restarts; ++restart) {
+    double xn2;
+    FV_TRY(V.dot(x, x, &xn2));
+    FV_TRY(V.lin(Vb.p, {{1.0 / std::sqrt(xn2), x}}));
+    std::fill(H.begin(), H.end(), 0.0);
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+      FV_TRY(A.apply(Vb.p + (size_t)j * n, w.p));
+      for (int pass = 0; pass < 2; ++pass) {
+        FV_TRY(launch_multidot<R>(g, Vb.p, n, j + 1, w.p, n, 1));
+        FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, j + 1, g->ws.scalars + 1, w.p, n));
+        FV_TRY(read_scalars(g, 1, j + 1, h.data()));
+        for (int i = 0; i <= j; ++i) {
+          if (!std::isfinite(h[i])) {
+            set_error("non-finite Gram-Schmidt coefficient");
+            return FV_ENAN;
+          }
+          H[(size_t)i * m + j] += h[i];
+        }
+      }
+      double wn2;
+      FV_TRY(V.dot(w.p, w.p, &wn2));
+      const double wn = std::sqrt(wn2);
+      H[(size_t)(j + 1) * m + j] = wn;
+      if (wn <= 1e-14 * std::fabs(H[(size_t)j * m + j]) || wn == 0.0) {
+        mm = j + 1;
+        break;
+      }
+      FV_TRY(V.lin(Vb.p + (size_t)(j + 1) * n, {{1.0 / wn, w.p}}));
+    }
+    if (!hessenberg_eigvals(mm, H.data(), m, hre, him)) {
+      set_error("Hessenberg QR did not converge");
+      return FV_ENOCONV;
+    }
+    ritz.resize(mm);
+    for (int i = 0; i < mm; ++i) ritz[i] = {hre[i], him[i]};
+    std::sort(ritz.begin(), ritz.end(), ritz_before);
+    // conjugate pairs: make them exact mirrors (+Im first)
+    for (int i = 0; i + 1 < mm; ++i)
+      if (ritz[i].im > 0 && std::fabs(ritz[i + 1].im + ritz[i].im) <= 1e-8 * std::fabs(ritz[i].im)) {
+        ritz[i + 1].re = ritz[i].re;
+        ritz[i + 1].im = -ritz[i].im;
+        ++i;
+      }
+    int nw = std::min(k, mm);
+    if (nw < mm && ritz[nw - 1].im > 0) ++nw;
+    // Ritz vectors (in the Krylov basis) and the Arnoldi residual estimates |h_{m+1,m}| |y_m|
+    Y.assign(nw, {});
+    const double hlast = (mm < m + 1) ? H[(size_t)mm * m + (mm - 1)] : 0.0;
+    bool all = true;
+    std::vector<double> est(nw);
+    for (int i = 0; i < nw; ++i) {
+      if (!hessenberg_eigvec(mm, H.data(), m, ritz[i].re, std::fabs(ritz[i].im), Y[i])) {
+        set_error("Ritz vector inverse iteration failed");
+        return FV_ENOCONV;
+      }
+      const double ymr = Y[i][2 * (mm - 1)], ymi = Y[i][2 * (mm - 1) + 1];
+      est[i] = std::fabs(hlast) * std::hypot(ymr, ymi);
+      const double mag = std::hypot(ritz[i].re, ritz[i].im);
+      if (!(est[i] <= o.tol * std::max(mag, 1e-300))) all = false;
+    }
+    rep->restarts = restart;
+    const bool last = all || mm < m || restart == o.max_restarts;
+    if (last) {
+      status = all || mm < m ? FV_OK : FV_ENOCONV;
+      nret = nw;
+      // Ritz vectors V y (Re, Im) into the output slots, then the FP64 residual ||A x - lam x|| / |lam|
+      DevBuf<R> X;
+      FV_TRY(X.alloc((size_t)(nw + 1) * n));
+      ycoef.assign(mm, 0.0);
+      for (int i = 0; i < nw; ++i) {
+        const bool cplx = ritz[i].im != 0.0;
+        const int src = i;
+        for (int part = 0; part < (cplx ? 2 : 1); ++part) {
+          const int slot = i + part;
+          if (slot >= nw) break;
+          for (int t = 0; t < mm; ++t) ycoef[t] = -Y[src][2 * t + part];
+          FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, ycoef.data(), sizeof(double) * mm, cudaMemcpyHostToDevice,
+                                  g->stream));
+          R* xs = X.p + (size_t)slot * n;
+          FV_TRY(V.zero(xs));
+          FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, xs, n));
+          FV_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        if (cplx) ++i;
+      }
+      for (int i = 0; i < nw; ++i) {
+        const bool cplx = ritz[i].im != 0.0;
+        const double lr = ritz[i].re, li = ritz[i].im;
+        R* xr = X.p + (size_t)i * n;
+        R* xi = cplx ? X.p + (size_t)(i + 1) * n : nullptr;
+        double nr2 = 0.0, ni2 = 0.0, res2 = 0.0;
+        FV_TRY(V.dot(xr, xr, &nr2));
+        FV_TRY(A.apply(xr, w.p));  // A xr - (lr xr - li xi)
+        if (cplx) {
+          FV_TRY(V.dot(xi, xi, &ni2));
+          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}, {li, xi}}));
+        } else {
+          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}}));
+        }
+        double t;
+        FV_TRY(V.dot(w.p, w.p, &t));
+        res2 += t;
+        if (cplx) {
+          FV_TRY(A.apply(xi, w.p));  // A xi - (lr xi + li xr)
+          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xi}, {-li, xr}}));
+          FV_TRY(V.dot(w.p, w.p, &t));
+          res2 += t;
+        }
+        const double xn = std::sqrt(nr2 + ni2), lam = std::hypot(lr, li);
+        const double rel = std::sqrt(res2) / (std::max(lam, 1e-300) * std::max(xn, 1e-300));
+        re[i] = lr;
+        im[i] = li;
+        if (i < 64) rep->residual[i] = rel;
+        if (cplx && i + 1 < nw) {
+          re[i + 1] = lr;
+          im[i + 1] = -li;
+          if (i + 1 < 64) rep->residual[i + 1] = rel;
+        }
+        // normalise the stored vector(s) to unit norm of the complex vector
+        const double sc = 1.0 / std::max(xn, 1e-300);
+        FV_TRY(V.lin(xr, {{sc, xr}}));
+        if (cplx) FV_TRY(V.lin(xi, {{sc, xi}}));
+        if (cplx) ++i;
+      }
+      if (vecs_out)
+        FV_CUDA(cudaMemcpyAsync(vecs_out, X.p, sizeof(R) * n * nw, cudaMemcpyDeviceToDevice, g->stream));
+      FV_CUDA(cudaStreamSynchronize(g->stream));
+      break;
+    }
+    // Chebyshev filter: wanted + guard Ritz values outside the ellipse, the rest inside
+    int nf = std::min(nw + o.guard, mm - 2);
+    if (nf < mm && nf >= 1 && ritz[nf - 1].im > 0) ++nf;
+    nf = std::max(nf, nw);
+    std::vector<Ritz> wanted(ritz.begin(), ritz.begin() + nf), unwanted(ritz.begin() + nf, ritz.end());
+    double d = 0, c2 = 0, rate = 0;
+    if (unwanted.empty()) {
+      d = ritz.back().re - 1.0;
+      c2 = 0.0;
+      rate = 1.0;
+    } else {
+      best_ellipse(wanted, unwanted, d, c2, rate);
+    }
+    int deg = o.min_degree;
+    if (rate > 1.0) deg = (int)std::ceil(std::log(1e8) / std::log(rate));
+    deg = std::max(o.min_degree, std::min(o.max_degree, deg));
+    if (restart < 256) rep->degrees[restart] = deg;
+    double lam_ref = -1e300;
+    for (auto& wv : wanted) lam_ref = std::max(lam_ref, wv.re);
+    // z = sum of the normalised wanted Ritz vectors (real part, or imaginary part of the -Im partner)
+    ycoef.assign(mm, 0.0);
+    for (int i = 0; i < nw; ++i) {
+      const bool cplx = ritz[i].im != 0.0;
+      for (int part = 0; part < (cplx ? 2 : 1); ++part) {
+        double nrm = 0.0;
+        for (int t = 0; t < mm; ++t) nrm += Y[i][2 * t + part] * Y[i][2 * t + part];
+        nrm = std::sqrt(nrm);
+        if (nrm > 0)
+          for (int t = 0; t < mm; ++t) ycoef[t] -= Y[i][2 * t + part] / nrm;
+      }
+      if (cplx) ++i;
+    }
+    FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, ycoef.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, g->stream));
+    R* z = y0.p;
+    FV_TRY(V.zero(z));
+    FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, z, n));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    // three-term recurrence: y1 = tau1 (A - d) y0; y_{j+1} = 2 tau_{j+1} (A - d) y_j - c2 tau_j tau_{j+1} y_{j-1}
+    const double s = lam_ref - d;
+    double tau = 1.0 / s;
+    R* yp = y0.p;  // y_{j-1}
+    R* yc = y1.p;  // y_j
+    FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yp, nullptr, tau, tau * (sigma - d), 0.0, yc));
+    ++mv;
+    for (int j = 1; j < deg; ++j) {
+      const double tn = 1.0 / (2.0 * s - c2 * tau);
+      // y_{j+1} overwrites y_{j-1}
+      FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yc, yp, 2.0 * tn, 2.0 * tn * (sigma - d), -c2 * tau * tn, yp));
+      ++mv;
+      std::swap(yp, yc);
+      tau = tn;
+      if (j % 16 == 0) {
+        double nn;
+        FV_TRY(V.dot(yc, yc, &nn));
+        nn = std::sqrt(nn);
+        if (nn > 1e30 || nn < 1e-30) {
+          FV_TRY(V.lin(yc, {{1.0 / nn, yc}}));
+          FV_TRY(V.lin(yp, {{1.0 / nn, yp}}));
+        }
+      }
+    }
+    if (yc != y0.p) FV_TRY(V.copy(y0.p, yc));
+    x = y0.p;
+  }
+  rep->matvecs = mv;
+  rep->nconv = nret;
+  rep->status = status;
+  for (int i = 0; i < nret && i < 64; ++i) {
+    const double sc = Gr > 0.0 ? 1.0 / std::sqrt(Gr) : 0.0;
+    rep->lam_scaled_re[i] = re[i] * sc;
+    rep->lam_scaled_im[i] = im[i] * sc;
+  }
+  rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return status;
+}
+
+}  // namespace fv
+
+extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, const fv_arnoldi_opts* opts, double* re,
+                               double* im, void* vecs, fv_arnoldi_report* report) {
+  if (!g || !q || !re || !im) return invalid("null argument");
+  fv_arnoldi_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fv_arnoldi_default_opts(&o);
+  if (k < 1 || o.m > 200 || k + o.guard + 2 > o.m || o.min_degree < 1 || o.max_degree < o.min_degree ||
+      o.max_restarts < 0 || k > 63)
+    return invalid("bad Arnoldi options (need 1 <= k <= 63, k + guard + 2 <= m <= 200)");
+  if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
+  fv_arnoldi_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  const int st = (o.precision == FV_FP64) ? arnoldi_impl<double>(g, k, Gr, q, o, re, im, vecs, &rep)
+                                          : arnoldi_impl<float>(g, k, Gr, q, o, re, im, vecs, &rep);
+  rep.status = st;
+  if (report) *report = rep;
+  return st;
+}

@@ -1,0 +1,171 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cube_fv.h"
+
+namespace fv {
+
+constexpr int kMaxN = 1024;
+
+// Device view of the metric arrays of one precision (all pointers into one device buffer).
+//   idx[d][c]  = 1 / width of cell c                    (c = 0..n-1)
+//   idc[d][f]  = 1 / centre spacing across face f       (f = 1..n-1); idc[d][0] = 2/width[0],
+//                idc[d][n] = 2/width[n-1] (half-cell distance from the first centre to the wall)
+//   wl[d][f], wr[d][f] = weights of cells f-1 and f in the linear interpolation to face f
+template <typename R>
+struct Geo {
+  int n[3];
+  const R* idx[3];
+  const R* idc[3];
+  const R* wl[3];
+  const R* wr[3];
+};
+
+// Fast-diagonalisation data of one precision: per axis the forward matrix Finv (mode x cell,
+// E^-1 = Y^T W^1/2), the backward matrix E (cell x mode, W^-1/2 Y) and the eigenvalues lam
+// (lam[0] = 0 is the constant mode).
+template <typename R>
+struct FdmDev {
+  const R* Einv[3];
+  const R* E[3];
+  const R* lam[3];
+};
+
+struct Workspace {
+  // per precision (0 = FP64, 1 = FP32): J.v output (4N), two transform buffers (N each), potential (N)
+  void* Y[2] = {nullptr, nullptr};
+  void* t0[2] = {nullptr, nullptr};
+  void* t1[2] = {nullptr, nullptr};
+  double* partials = nullptr;      // reduction partials
+  double* scalars = nullptr;       // device scalars (reduction results)
+  double* host_scalars = nullptr;  // pinned host mirror
+};
+
+}  // namespace fv
+
+namespace fv {
+struct ProfRecord {
+  int kind;
+  cudaEvent_t start, stop;
+};
+struct Profiler {
+  bool enabled = false;
+  std::vector<ProfRecord> records;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+};
+}  // namespace fv
+
+struct fv_grid_s {
+  int nx, ny, nz;
+  size_t N;  // nx*ny*nz
+  double Pr;
+  cudaStream_t stream;
+  std::vector<double> xf[3];
+  // metrics and FDM data, both precisions
+  void* metric_buf[2] = {nullptr, nullptr};
+  fv::Geo<double> geo64;
+  fv::Geo<float> geo32;
+  fv::FdmDev<double> fdm64;
+  fv::FdmDev<float> fdm32;
+  fv::Workspace ws;
+  double sigma_default;
+  double min_width[3];
+  mutable fv::Profiler prof;
+};
+
+namespace fv {
+
+// ------------------------------------------------------------------ error reporting
+void set_error(const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);
+#define FV_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return fv::cuda_status(_e, #call); \
+  } while (0)
+#define FV_TRY(expr)            \
+  do {                          \
+    int _s = (expr);            \
+    if (_s != FV_OK) return _s; \
+  } while (0)
+
+// ------------------------------------------------------------------ measurement
+enum { PROF_STENCIL = 0, PROF_DIVERGENCE = 1, PROF_TRANSFORM = 2, PROF_CORRECT = 3, PROF_REDUCE = 4, PROF_VECTOR = 5 };
+// Records a CUDA event pair around the launches in its scope when profiling is enabled.
+struct ProfScope {
+  const fv_grid_s* g;
+  cudaEvent_t stop = nullptr;
+  ProfScope(const fv_grid_s* grid, int kind);
+  ~ProfScope();
+};
+
+// ------------------------------------------------------------------ kernels (launchers)
+// Stencils (kernels_stencil.cu)
+template <typename R>
+int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F);
+template <typename R>
+int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);
+template <typename R>
+int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs);
+// out = alpha (Y - G phi) + beta v + gamma w   (velocity; T without G phi).  v, w may be null.
+template <typename R>
+int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, const R* v, double beta,
+                   const R* w, double gamma, R* out);
+
+// Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
+template <typename R>
+int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp);
+
+// BLAS-1 and reductions (kernels_blas.cu).  Results land in g->ws.scalars[slot...].
+template <typename R>
+int launch_dot(const fv_grid_s* g, const R* a, const R* b, size_t n, int slot);
+template <typename R>
+int launch_multidot(const fv_grid_s* g, const R* V, size_t ldv, int m, const R* w, size_t n, int slot);
+template <typename R>
+int launch_maxabs(const fv_grid_s* g, const R* a, size_t n, int slot);
+// out = sum_i c[i] x[i], i < nvec <= 4 (x may alias out)
+template <typename R>
+int launch_lincomb(const fv_grid_s* g, size_t n, int nvec, const double* c, const R* const* x, R* out);
+// w <- w - V h   (V: m vectors with leading dimension ldv; h device FP64)
+template <typename R>
+int launch_subtract_basis(const fv_grid_s* g, const R* V, size_t ldv, int m, const double* h, R* w, size_t n);
+int launch_convert(const fv_grid_s* g, size_t n, const double* src, float* dst);
+int launch_convert(const fv_grid_s* g, size_t n, const float* src, double* dst);
+template <typename R>
+int launch_fill_normal(const fv_grid_s* g, unsigned long long seed, R* out);
+
+constexpr int kReduceBlocks = 1024;
+constexpr int kMaxScalars = 512;
+
+// host scalar readback: copies `count` scalars starting at `slot` and synchronises
+int read_scalars(const fv_grid_s* g, int slot, int count, double* out);
+
+// ------------------------------------------------------------------ host linear algebra (host_linalg.cpp)
+// Symmetric tridiagonal eigen-decomposition (implicit QR with Wilkinson shifts).
+// d: diagonal (n), e: off-diagonal (n-1); on return d holds eigenvalues, Q (n*n, row-major,
+// column j = eigenvector j).  Returns false if it fails to converge.
+bool tridiag_eig(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Q);
+// Eigenvalues of a real upper Hessenberg matrix (m x m, row-major, leading dimension ld) by complex
+// single-shift QR.  Returns false on non-convergence.
+bool hessenberg_eigvals(int m, const double* H, int ld, std::vector<double>& re, std::vector<double>& im);
+// Eigenvector of H for eigenvalue (re, im) by inverse iteration (complex).  y: 2*m (re, im interleaved).
+bool hessenberg_eigvec(int m, const double* H, int ld, double re, double im, std::vector<double>& y);
+// Solve a small dense system A x = b (n x n row-major) with partial pivoting; false if singular.
+bool dense_solve(int n, std::vector<double> A, std::vector<double>& b);
+// Least squares min || H y - beta e1 || for the (j+1) x j Hessenberg of GMRES (row-major, ld).
+void hessenberg_lstsq(int j, const double* H, int ld, double beta, std::vector<double>& y, double* resid);
+
+// ------------------------------------------------------------------ drivers (fv_api.cpp)
+template <typename R>
+int jvp_project(fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);
+template <typename R>
+int chebyshev_step(fv_grid_s* g, double Gr, double sigma, const R* q, const R* y, const R* yprev,
+                   double alpha, double beta, double gamma, R* out);
+
+}  // namespace fv

@@ -1,0 +1,207 @@
+"""GPU parity: every entry point of libcubefv.so against the FP64 oracle on identical seeded inputs.
+
+Tolerances (norm-wise, per field: max|gpu - oracle| / max|oracle|):
+* FP64 paths: 1e-12 for the stencils and the projection (different summation order only; the
+  worst cancellation is the diffusion term ~ 4 max|v| / h_min^2 against results of the same order).
+* FP32 paths: inputs are rounded to FP32 first and the oracle runs in FP64 on the rounded values.
+  The stencil sums ~40 products with unit round-off u = 2^-24; the fast-diagonalisation solve applies
+  six dense n x n transforms whose rounding grows like sqrt(n) u each, so the projected fields carry
+  ~6 sqrt(n) u ~ 6e-6 at n = 256.  Bounds: 2e-5 (stencil), 5e-5 (projection / fused path).
+"""
+import numpy as np
+import pytest
+
+import oracle.discretisation as D
+from oracle.projection import Projector
+from paper_2210_08816_gb300 import seeded
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PR = 0.71
+TOL64 = 1e-12
+TOL32_STENCIL = 2e-5
+TOL32_PROJ = 5e-5
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_08816_gb300 import build
+    build.build()
+    from paper_2210_08816_gb300 import fv as _fv
+    _fv.lib()
+    return _fv
+
+
+def dev(api, dtype):
+    return torch.tensor(np.stack(api), dtype=dtype, device="cuda").contiguous().view(-1)
+
+
+def host(t, shape):
+    a = t.view(4, *shape).double().cpu().numpy()
+    return [a[c] for c in range(4)]
+
+
+def rel(a, b):
+    return max(float(np.max(np.abs(a[c] - b[c]))) / max(float(np.max(np.abs(b[c]))), 1e-300) for c in range(4))
+
+
+def state(og, seed, sigma=0.5, project=True):
+    """Seeded base state: conduction + projected N(0, sigma^2) perturbation (exchange layout)."""
+    q = D.from_api(og, seeded.normal_fields(seed, og.shape, sigma))
+    if project:
+        q = Projector(og).full(q)
+    q[3] = q[3] + (1.0 - og.axes[0].xc)[None, None, :]
+    return D.to_api(og, q)
+
+
+def vector(og, seed, sigma=1.0):
+    return D.to_api(og, D.from_api(og, seeded.normal_fields(seed, og.shape, sigma)))
+
+
+def round32(api):
+    return [a.astype(np.float32).astype(np.float64) for a in api]
+
+
+GRIDS = [((7, 5, 3), 0.0), ((17, 13, 11), 1.5), ((32, 32, 32), 1.5), ((2, 2, 2), 0.0), ((64, 48, 40), 1.5),
+         ((130, 3, 5), 0.0)]
+
+
+@pytest.mark.parametrize("shape,stretch", GRIDS)
+def test_residual_fp64(fv, shape, stretch):
+    og = D.Grid(*shape, stretch=stretch, Pr=PR)
+    g = fv.Grid(*shape, stretch=stretch, Pr=PR)
+    q = state(og, 1)
+    Gr = 3.0e4
+    F = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_residual(g, Gr, dev(q, torch.float64), F)
+    assert rel(host(F, og.shape), D.residual(og, Gr, q)) <= TOL64
+
+
+@pytest.mark.parametrize("shape,stretch", GRIDS)
+def test_jvp_fp64_and_fp32(fv, shape, stretch):
+    og = D.Grid(*shape, stretch=stretch, Pr=PR)
+    g = fv.Grid(*shape, stretch=stretch, Pr=PR)
+    q, v = state(og, 2), vector(og, 3)
+    Gr = 5.0e4
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_jvp(g, fv.FV_FP64, Gr, dev(q, torch.float64), dev(v, torch.float64), out)
+    assert rel(host(out, og.shape), D.jvp(og, Gr, q, v)) <= TOL64
+    q32, v32 = round32(q), round32(v)
+    out32 = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    fv.fv_jvp(g, fv.FV_FP32, Gr, dev(q32, torch.float32), dev(v32, torch.float32), out32)
+    assert rel(host(out32, og.shape), D.jvp(og, Gr, q32, v32)) <= TOL32_STENCIL
+
+
+@pytest.mark.parametrize("shape,stretch", GRIDS)
+def test_project_fp64_and_fp32(fv, shape, stretch):
+    og = D.Grid(*shape, stretch=stretch, Pr=PR)
+    g = fv.Grid(*shape, stretch=stretch, Pr=PR)
+    v = vector(og, 4)
+    ref = Projector(og).api(v)
+    t = dev(v, torch.float64)
+    it, div = fv.fv_project(g, fv.FV_FP64, t, max_it=1, want_div=True)
+    assert it == 1 and div <= 1e-12
+    assert rel(host(t, og.shape), ref) <= TOL64
+    v32 = round32(v)
+    ref32 = Projector(og).api(v32)
+    t32 = dev(v32, torch.float32)
+    it, div = fv.fv_project(g, fv.FV_FP32, t32, max_it=1, want_div=True)
+    assert div <= 1e-4
+    assert rel(host(t32, og.shape), ref32) <= TOL32_PROJ
+
+
+@pytest.mark.parametrize("shape,stretch", [((17, 13, 11), 1.5), ((40, 40, 40), 1.5), ((3, 4, 5), 0.0)])
+@pytest.mark.parametrize("sigma", [0.0, -750.0])
+def test_jvp_project_fused(fv, shape, stretch, sigma):
+    og = D.Grid(*shape, stretch=stretch, Pr=PR)
+    g = fv.Grid(*shape, stretch=stretch, Pr=PR)
+    q, v = state(og, 5), vector(og, 6)
+    Gr = 1.0e5
+    P = Projector(og)
+    qf, vf = D.from_api(og, q), D.from_api(og, v)
+    J = D.jvp_full(og, Gr, qf, vf)
+    ref = P.full([J[c] - sigma * vf[c] for c in range(4)])
+    ref = D.to_api(og, [ref[c] + sigma * vf[c] for c in range(4)])
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_jvp_project(g, fv.FV_FP64, Gr, sigma, dev(q, torch.float64), dev(v, torch.float64), out)
+    assert rel(host(out, og.shape), ref) <= TOL64
+    q32, v32 = round32(q), round32(v)
+    qf, vf = D.from_api(og, q32), D.from_api(og, v32)
+    J = D.jvp_full(og, Gr, qf, vf)
+    ref = P.full([J[c] - sigma * vf[c] for c in range(4)])
+    ref = D.to_api(og, [ref[c] + sigma * vf[c] for c in range(4)])
+    out32 = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    fv.fv_jvp_project(g, fv.FV_FP32, Gr, sigma, dev(q32, torch.float32), dev(v32, torch.float32), out32)
+    assert rel(host(out32, og.shape), ref) <= TOL32_PROJ
+
+
+def test_dot_axpby_deterministic(fv):
+    shape = (33, 17, 9)
+    og = D.Grid(*shape)
+    g = fv.Grid(*shape)
+    a, b = vector(og, 7), vector(og, 8)
+    ta, tb = dev(a, torch.float64), dev(b, torch.float64)
+    r1 = fv.fv_dot(g, fv.FV_FP64, ta, tb)
+    r2 = fv.fv_dot(g, fv.FV_FP64, ta, tb)
+    assert r1 == r2
+    ref = sum(float(np.sum(a[c] * b[c])) for c in range(4))
+    assert abs(r1 - ref) <= 1e-12 * sum(float(np.sum(np.abs(a[c] * b[c]))) for c in range(4))
+    fv.fv_axpby(g, fv.FV_FP64, 2.0, ta, -0.5, tb)
+    got = host(tb, og.shape)
+    assert rel(got, [2.0 * a[c] - 0.5 * b[c] for c in range(4)]) <= 1e-15
+    t32 = dev(a, torch.float32)
+    assert fv.fv_dot(g, fv.FV_FP32, t32, t32) == pytest.approx(sum(float(np.sum(a[c] ** 2)) for c in range(4)),
+                                                               rel=1e-6)
+
+
+def test_full_size_256_fp32_fused_matches_oracle(fv):
+    """256^3 tanh-stretched, Gr = 2e8: the bench's workload and launch configuration."""
+    shape, Gr = (256, 256, 256), 2.0e8
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = state(og, 100, sigma=50.0, project=False)   # synthetic base flow (divergence not required for J.v)
+    v = vector(og, 101)
+    q32, v32 = round32(q), round32(v)
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    fv.fv_jvp_project(g, fv.FV_FP32, Gr, 0.0, dev(q32, torch.float32), dev(v32, torch.float32), out)
+    got = host(out, og.shape)
+    del out
+    ref = Projector(og).api(D.jvp(og, Gr, q32, v32))
+    assert rel(got, ref) <= TOL32_PROJ
+
+
+def test_errors_are_status_codes(fv):
+    with pytest.raises(fv.FvError) as e:
+        fv.Grid(1, 4, 4)
+    assert e.value.status == fv.FV_EINVAL
+    g = fv.Grid(4, 4, 4)
+    a = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_jvp_project(g, fv.FV_FP64, 1.0, 0.0, a, a, a)
+    assert e.value.status == fv.FV_EINVAL
+    with pytest.raises(fv.FvError):
+        fv.fv_jvp(g, 7, 1.0, a, a, torch.zeros_like(a))
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_fused_recurrence_step(fv, prec_name):
+    shape, Gr, sigma = (20, 14, 9), 8.0e4, -900.0
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q, v, w = state(og, 9), vector(og, 10), vector(og, 11)
+    prec, dt, tol = ((fv.FV_FP64, torch.float64, TOL64) if prec_name == "fp64"
+                     else (fv.FV_FP32, torch.float32, TOL32_PROJ))
+    if prec_name == "fp32":
+        q, v, w = round32(q), round32(v), round32(w)
+    alpha, beta, gamma = 0.37, -1.9, 0.55
+    P = Projector(og)
+    qf, vf, wf = D.from_api(og, q), D.from_api(og, v), D.from_api(og, w)
+    J = D.jvp_full(og, Gr, qf, vf)
+    A = P.full([J[c] - sigma * vf[c] for c in range(4)])
+    ref = D.to_api(og, [alpha * (A[c] + sigma * vf[c]) + beta * vf[c] + gamma * wf[c] for c in range(4)])
+    tw = dev(w, dt)
+    fv.fv_jvp_project_lincomb(g, prec, Gr, sigma, dev(q, dt), dev(v, dt), tw, alpha, beta, gamma, tw)
+    assert rel(host(tw, og.shape), ref) <= tol

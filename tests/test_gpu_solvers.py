@@ -1,0 +1,153 @@
+"""GPU Newton and Chebyshev-Arnoldi drivers (through the C-ABI) against the oracle.
+
+* FP64 Newton reaches the oracle's steady state (both solve P F = 0 to round-off; the states agree
+  to 1e-9 in max-norm, the residual tolerance divided by the smallest eigenvalue magnitude).
+* Mixed Newton (FP32 Krylov, FP64 residual) refines to the FP64 state within 1e-8 max-norm.
+* FP64 Arnoldi: Gr = 0 closed-form temperature spectrum, and agreement with the oracle's
+  Chebyshev-Arnoldi at Gr > 0 (both converged to 1e-9 residual: eigenvalues to 1e-8).
+* Mixed Arnoldi: leading eigenvalue within 1e-6 of the FP64 one; its Ritz vectors certified by the
+  oracle's own FP64 residual ||P J x - lam x|| / (|lam| ||x||).
+"""
+import numpy as np
+import pytest
+
+import oracle.discretisation as D
+from oracle import diagnostics as DG
+from oracle import solvers as SV
+from oracle.projection import Projector
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+PR = 0.71
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_08816_gb300 import build
+    build.build()
+    from paper_2210_08816_gb300 import fv as _fv
+    _fv.lib()
+    return _fv
+
+
+def dev(api):
+    return torch.tensor(np.stack(api), dtype=torch.float64, device="cuda").contiguous().view(-1)
+
+
+def host(t, shape):
+    a = t.view(4, *shape).double().cpu().numpy()
+    return [a[c] for c in range(4)]
+
+
+def maxrel(a, b):
+    return max(float(np.max(np.abs(a[c] - b[c]))) for c in range(4)) / max(float(np.max(np.abs(b[c]))) for c in range(4))
+
+
+def conduction_api(og):
+    return D.to_api(og, D.conduction_state(og))
+
+
+def test_newton_fp64_matches_oracle(fv):
+    shape, Gr = (10, 8, 6), 1.2e4
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    q_ref, rep_ref = SV.newton_steady(og, Gr, D.conduction_state(og), tol=1e-11)
+    assert rep_ref["status"] == "converged"
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = dev(conduction_api(og))
+    o = fv.fv_newton_default_opts()
+    o.tol = 1e-11
+    st, rep = fv.newton_steady(g, Gr, q, o)
+    assert st == fv.FV_OK, rep.history[:rep.newton_steps + 1]
+    got = host(q, og.shape)
+    assert maxrel(got, D.to_api(og, q_ref)) <= 1e-9
+    assert max(DG.symmetry_measures(og, got[3])) <= 1e-9      # Section 2: symmetric steady flow
+
+
+def test_newton_mixed_refines_to_fp64(fv):
+    shape, Gr = (16, 16, 16), 1.0e5
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    res = {}
+    for prec in (fv.FV_FP64, fv.FV_FP32):
+        q = dev(conduction_api(og))
+        o = fv.fv_newton_default_opts()
+        o.precision = prec
+        o.tol = 1e-12
+        o.max_newton = 30
+        o.gr_start = 1.25e4
+        o.gr_ratio = 2.0
+        st, rep = fv.newton_steady(g, Gr, q, o)
+        assert st == fv.FV_OK, (prec, list(rep.history[:rep.newton_steps + 1]))
+        res[prec] = host(q, og.shape)
+    assert maxrel(res[fv.FV_FP32], res[fv.FV_FP64]) <= 1e-8
+    # certificate with the oracle's own operators
+    P = Projector(og)
+    r = P.full(D.residual_full(og, Gr, D.from_api(og, res[fv.FV_FP32])))
+    scale = max(float(np.max(np.abs(a))) for a in D.residual_full(og, Gr, D.conduction_state(og)))
+    assert max(float(np.max(np.abs(a))) for a in r) <= 1e-9 * scale
+
+
+def test_newton_32cube_uniform_config(fv):
+    """32^3 uniform, Pr = 0.71, Gr = 1e5 (continuation from 1.25e4), inner solves to 1e-10."""
+    shape, Gr = (32, 32, 32), 1.0e5
+    og = D.Grid(*shape, stretch=0.0, Pr=PR)
+    g = fv.Grid(*shape, stretch=0.0, Pr=PR)
+    q = dev(conduction_api(og))
+    o = fv.fv_newton_default_opts()
+    o.gr_start, o.gr_ratio = 1.25e4, 2.0
+    st, rep = fv.newton_steady(g, Gr, q, o)
+    assert st == fv.FV_OK
+    got = host(q, og.shape)
+    P = Projector(og)
+    r = P.full(D.residual_full(og, Gr, D.from_api(og, got)))
+    assert max(float(np.max(np.abs(a))) for a in r) <= 1e-9 * rep.residual0
+    assert max(DG.symmetry_measures(og, got[3])) <= 1e-9
+    assert DG.nusselt_hot(og, got[3]) < -1.0
+
+
+def test_arnoldi_fp64_gr0_closed_form(fv):
+    shape = (10, 8, 6)
+    og = D.Grid(*shape, stretch=0.0, Pr=PR)
+    g = fv.Grid(*shape, stretch=0.0, Pr=PR)
+    q = dev(conduction_api(og))
+    o = fv.fv_arnoldi_default_opts()
+    o.tol = 1e-10
+    st, lam, rep = fv.arnoldi_leading(g, 4, 0.0, q, o)
+    assert st == fv.FV_OK
+    l1 = lambda n, j: 4.0 * n * n * np.sin(j * np.pi / (2 * n)) ** 2
+    expect = sorted((-(l1(10, a) + l1(8, b) + l1(6, c)) / PR for a in range(1, 4) for b in range(4) for c in range(4)),
+                    reverse=True)[:4]
+    assert np.allclose([z.real for z in lam[:4]], expect, rtol=1e-9, atol=0)
+
+
+def test_arnoldi_fp64_and_mixed_vs_oracle(fv):
+    shape, Gr = (8, 7, 6), 1.2e4
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    q_ref, _ = SV.newton_steady(og, Gr, D.conduction_state(og), tol=1e-11)
+    x0 = np.random.default_rng(3).standard_normal(D.n_unknowns(og))
+    lam_ref, _, info = SV.leading_eigenvalues(og, Gr, q_ref, k=4, m=20, seed_vector=x0, tol=1e-9)
+    assert info["converged"]
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = dev(D.to_api(og, q_ref))
+    o = fv.fv_arnoldi_default_opts()
+    o.tol = 1e-9
+    st, lam, rep = fv.arnoldi_leading(g, 4, Gr, q, o)
+    assert st == fv.FV_OK
+    k = min(len(lam), len(lam_ref))
+    assert np.allclose(np.array(lam[:k]), lam_ref[:k], rtol=1e-8, atol=0), (lam, lam_ref)
+    # mixed: FP32 Krylov vectors, FP64 Hessenberg / Gram-Schmidt coefficients
+    o.precision = fv.FV_FP32
+    o.tol = 1e-6
+    vecs = torch.empty((4 + 1) * g.n, dtype=torch.float32, device="cuda")
+    st, lam32, rep32 = fv.arnoldi_leading(g, 4, Gr, q, o, vecs=vecs)
+    assert st == fv.FV_OK
+    assert abs(lam32[0] - lam_ref[0]) <= 1e-6 * abs(lam_ref[0])
+    # certify the leading Ritz vector with the oracle's FP64 operator
+    x = host(vecs[:g.n], og.shape)
+    A = SV.projected_jacobian(og, Gr, q_ref)
+    xv = D.pack(D.from_api(og, x))
+    if lam32[0].imag == 0.0:
+        r = A(xv) - lam32[0].real * xv
+        assert np.linalg.norm(r) <= 1e-5 * abs(lam32[0]) * np.linalg.norm(xv)
