@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--grid", type=int, default=256)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-eigen", action="store_true", help="skip the 32^3 time-to-eigenpair leg")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     p.add_argument("--cpu-sample-only", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -267,6 +269,18 @@ def gpu_arm(args, ws, rank, local):
     breakdown = {k: {"ms_per_step": round(v[0] / K, 4), "launches_per_step": v[1] / K} for k, v in prof.items()}
 
     # e2e through the C-ABI with host buffers: H2D of the step's input vector, the step, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream)
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = fp64_leg(fv, g, q64, y0_64, y1_64, sigma, K, ws, device, stream)
+    return finish(args, ws, rank, n, value, K, W, ms_step, e2e, launches, roof, hbm_stencil, step_bytes, breakdown,
+                  fp64, clocks, g, device)
+
+
+def e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream):
+    import torch
     host_in = ya.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     Ke = max(3, min(K, 10))
@@ -281,6 +295,7 @@ def gpu_arm(args, ws, rank, local):
     for _ in range(Ke):
         ya.copy_(host_in, non_blocking=True)
         fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb)
+        fv.fv_dot(g, fv.FV_FP32, yb, yb)
         host_out.copy_(yb, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
@@ -288,8 +303,11 @@ def gpu_arm(args, ws, rank, local):
     e2e = {"value": round(ws * Ke / (e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": host_in.numel() * 4,
            "d2h_bytes_per_step": host_out.numel() * 4, "steps": Ke}
     del host_in, host_out
+    return e2e
 
-    # plain FP64 form on the same GPU (same step, FP64 everywhere)
+
+def fp64_leg(fv, g, q64, y0_64, y1_64, sigma, K, ws, device, stream):
+    """Plain FP64 form on the same GPU (same step, FP64 everywhere)."""
     za, zb = y0_64.clone(), y1_64.clone()
     run_steps(fv, g, fv.FV_FP64, q64, za, zb, 2, stream, sigma)
     K64 = max(3, min(K, 5))
@@ -297,7 +315,13 @@ def gpu_arm(args, ws, rank, local):
     ms64 = max_over_ranks(ws, ms64, device)
     fp64 = {"value": round(ws * K64 / (ms64 / 1e3), 3), "ms_per_step": round(ms64 / K64, 3), "steps": K64}
     del za, zb
+    return fp64
 
+
+def finish(args, ws, rank, n, value, K, W, ms_step, e2e, launches, roof, hbm_stencil, step_bytes, breakdown, fp64,
+           clocks, g, device):
+    import torch
+    from paper_2210_08816_gb300 import fv
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -312,7 +336,6 @@ def gpu_arm(args, ws, rank, local):
         "step_algorithmic_bytes": step_bytes, "kernel_breakdown": breakdown, "fp64_plain": fp64,
         "clocks": clocks,
     }
-    del q, ya, yb, q64, y0_64, y1_64
     g.close()
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_eigen:

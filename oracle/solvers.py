@@ -17,7 +17,10 @@ Readings where the paper is silent:
   contains the unwanted Ritz values; it is picked from a confocal family by a
   small scan that maximises the slowest wanted damping rate.  The polynomial is
   T_n((z - d)/c) / T_n((lam_ref - d)/c), applied by its three-term recurrence in
-  real arithmetic with c^2 (which may be negative).
+  real arithmetic with c^2 (which may be negative).  The ellipse contains this
+  cycle's unwanted Ritz values and the far end of the spectrum (the Rayleigh
+  quotient of a short power iteration, pushed out by 5%): filtered restarts no
+  longer show that end, and T_n grows fast outside its ellipse.
 * P J vanishes on the gradient complement range(G), so on the full unknown
   space it has a spurious eigenvalue 0 that lies to the right of every wanted
   eigenvalue of a stable flow; round-off gradient components would be
@@ -268,7 +271,7 @@ def chebyshev_filter(A, y0, d, c2, lam_ref, degree):
 
 
 def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=200, min_degree=10,
-                      guard=2):
+                      guard=2, power_steps=30):
     """Leading k eigenpairs (largest real part) of A by Chebyshev-preconditioned Arnoldi.
 
     Returns (lam, X, info): lam complex (k or k+1 values when a conjugate pair
@@ -286,6 +289,16 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
     def Af(v):
         nmv[0] += 1
         return A(v)
+
+    # the far end of the spectrum: the largest-magnitude eigenvalue by power iteration (its Rayleigh
+    # quotient); filtered restarts stop showing it, and T_n grows fast outside the ellipse
+    z = x.copy()
+    lam_far = 0.0
+    for _ in range(power_steps):
+        y = Af(z)
+        lam_far = float(np.dot(z, y))
+        z = y / np.linalg.norm(y)
+    info["lam_far"] = lam_far
 
     for it in range(max_restarts + 1):
         V, H, mm = arnoldi(Af, x, m)
@@ -310,7 +323,10 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
         if nf < mm and abs(theta[nf - 1].imag) > 0 and np.isclose(theta[nf], np.conj(theta[nf - 1])):
             nf += 1
         nf = max(nf, nw)
-        wanted, unwanted = theta[:nf], theta[nf:]
+        wanted = theta[:nf]
+        # the ellipse contains this cycle's unwanted Ritz values and the far end of the spectrum
+        left = min(float(np.min(theta[nf:].real)), lam_far) if nf < mm else lam_far
+        unwanted = np.concatenate([theta[nf:], [complex(1.05 * left, 0.0)]])
         d, c2, rate = best_ellipse(wanted, unwanted)
         lam_ref = float(np.max(wanted.real))
         if rate > 1.0:

@@ -520,6 +520,7 @@ int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out) {
   for (int d = 0; d < 3; ++d)
     if (n[d] < 2 || n[d] > kMaxN) return invalid("grid size out of range [2, 1024]");
   if (!(desc->Pr > 0.0)) return invalid("Pr must be positive");
+  if (4.0 * n[0] * n[1] * (double)n[2] >= 2147483647.0) return invalid("4*nx*ny*nz must be below 2^31");
   const double* given[3] = {desc->xf, desc->yf, desc->zf};
   fv_grid_s* g = new fv_grid_s();
   g->nx = n[0];
@@ -905,6 +906,22 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   R* x = y0.p;
   FV_TRY(launch_fill_normal<R>(g, o.seed, x));
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
+  // far end of the spectrum: Rayleigh quotient of a short power iteration (filtered restarts stop
+  // showing it, and the Chebyshev polynomial grows fast outside its ellipse)
+  double lam_far = 0.0;
+  {
+    R* z = y1.p;
+    double zn2;
+    FV_TRY(V.dot(x, x, &zn2));
+    FV_TRY(V.lin(z, {{1.0 / std::sqrt(zn2), x}}));
+    for (int it = 0; it < 30; ++it) {
+      FV_TRY(A.apply(z, w.p));
+      FV_TRY(V.dot(z, w.p, &lam_far));
+      double wn2;
+      FV_TRY(V.dot(w.p, w.p, &wn2));
+      FV_TRY(V.lin(z, {{1.0 / std::sqrt(wn2), w.p}}));
+    }
+  }
   std::vector<double> H((size_t)(m + 1) * m), h(m + 1), hre, him, ycoef;
   std::vector<std::vector<double>> Y;
   std::vector<Ritz> ritz;
@@ -944,16 +961,39 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       set_error("Hessenberg QR did not converge");
       return FV_ENOCONV;
     }
-    ritz.resize(mm);
-    for (int i = 0; i < mm; ++i) ritz[i] = {hre[i], him[i]};
-    std::sort(ritz.begin(), ritz.end(), ritz_before);
-    // conjugate pairs: make them exact mirrors (+Im first)
-    for (int i = 0; i + 1 < mm; ++i)
-      if (ritz[i].im > 0 && std::fabs(ritz[i + 1].im + ritz[i].im) <= 1e-8 * std::fabs(ritz[i].im)) {
-        ritz[i + 1].re = ritz[i].re;
-        ritz[i + 1].im = -ritz[i].im;
-        ++i;
+    // H is real: pair each +Im value with its nearest -Im partner and make the pair exact mirrors
+    // (the complex QR returns them with slightly different real parts), then sort (+Im first)
+    ritz.clear();
+    {
+      std::vector<bool> used(mm, false);
+      for (int i = 0; i < mm; ++i) {
+        if (used[i]) continue;
+        used[i] = true;
+        if (him[i] == 0.0) {
+          ritz.push_back({hre[i], 0.0});
+          continue;
+        }
+        int best = -1;
+        double bd = 1e300;
+        for (int j2 = 0; j2 < mm; ++j2)
+          if (!used[j2] && him[j2] * him[i] < 0.0) {
+            const double dd = std::hypot(hre[j2] - hre[i], him[j2] + him[i]);
+            if (dd < bd) {
+              bd = dd;
+              best = j2;
+            }
+          }
+        if (best >= 0) {
+          used[best] = true;
+          const double r = 0.5 * (hre[i] + hre[best]), a = 0.5 * (std::fabs(him[i]) + std::fabs(him[best]));
+          ritz.push_back({r, a});
+          ritz.push_back({r, -a});
+        } else {
+          ritz.push_back({hre[i], him[i]});
+        }
       }
+    }
+    std::sort(ritz.begin(), ritz.end(), ritz_before);
     int nw = std::min(k, mm);
     if (nw < mm && ritz[nw - 1].im > 0) ++nw;
     // Ritz vectors (in the Krylov basis) and the Arnoldi residual estimates |h_{m+1,m}| |y_m|
@@ -1045,14 +1085,11 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     if (nf < mm && nf >= 1 && ritz[nf - 1].im > 0) ++nf;
     nf = std::max(nf, nw);
     std::vector<Ritz> wanted(ritz.begin(), ritz.begin() + nf), unwanted(ritz.begin() + nf, ritz.end());
+    double left = lam_far;
+    for (auto& u : unwanted) left = std::min(left, u.re);
+    unwanted.push_back({1.05 * left, 0.0});
     double d = 0, c2 = 0, rate = 0;
-    if (unwanted.empty()) {
-      d = ritz.back().re - 1.0;
-      c2 = 0.0;
-      rate = 1.0;
-    } else {
-      best_ellipse(wanted, unwanted, d, c2, rate);
-    }
+    best_ellipse(wanted, unwanted, d, c2, rate);
     int deg = o.min_degree;
     if (rate > 1.0) deg = (int)std::ceil(std::log(1e8) / std::log(rate));
     deg = std::max(o.min_degree, std::min(o.max_degree, deg));

@@ -2,8 +2,13 @@
 // axpys of BiCGstab(2), GMRES and the Chebyshev-preconditioned Arnoldi iteration, Section 1).
 //
 // Reductions are two-pass and deterministic: a fixed grid of kReduceBlocks blocks, each summing a fixed
-// contiguous chunk in a fixed order (FP64 accumulation, warp-shuffle tree), then one block summing the
-// partials in a fixed order.  Reruns are bit-identical.
+// contiguous chunk in a fixed order (warp-shuffle tree in FP64), then one block summing the partials in a
+// fixed order.  Reruns are bit-identical.
+//
+// Accumulation precision.  FP64 vectors accumulate in FP64.  For FP32 vectors each thread keeps a
+// compensated pair (hi, lo) of floats: the product a*b is split exactly into p + e with an FMA and added
+// by Knuth's TwoSum, so a thread's partial carries ~44 significant bits before it is converted to FP64.
+// This keeps the inner products at FP64-like accuracy on GB300, whose FP64 pipe is ~1/64 of FP32.
 #include "fv_internal.h"
 
 namespace fv {
@@ -55,13 +60,41 @@ __device__ __forceinline__ void chunk_of(size_t n, size_t& b, size_t& e) {
   e = b + L < n ? b + L : n;
 }
 
+// compensated float accumulator: value = hi + lo
+struct F2 {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_product(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // a*b = p + pe exactly
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);  // hi + p = s + err exactly
+    hi = s;
+    lo += err + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename R>
+__device__ __forceinline__ double dot_chunk(const R* __restrict__ a, const R* __restrict__ b, size_t s, size_t e) {
+  double acc = 0.0;
+  for (size_t t = s + threadIdx.x; t < e; t += kThreads) acc = fma((double)a[t], (double)b[t], acc);
+  return acc;
+}
+template <>
+__device__ __forceinline__ double dot_chunk<float>(const float* __restrict__ a, const float* __restrict__ b, size_t s,
+                                                   size_t e) {
+  F2 acc;
+  for (size_t t = s + threadIdx.x; t < e; t += kThreads) acc.add_product(a[t], b[t]);
+  return acc.value();
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_dot_partial(const R* __restrict__ a, const R* __restrict__ b, size_t n,
                                                            double* __restrict__ part) {
   size_t s, e;
   chunk_of(n, s, e);
-  double acc[1] = {0.0};
-  for (size_t t = s + threadIdx.x; t < e; t += kThreads) acc[0] += (double)a[t] * (double)b[t];
+  double acc[1] = {dot_chunk<R>(a, b, s, e)};
   double r[1];
   block_reduce<1, false>(acc, r);
   if (threadIdx.x == 0) part[blockIdx.x] = r[0];
@@ -71,8 +104,15 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_maxabs_partial(const R* __restrict__ a, size_t n, double* __restrict__ part) {
   size_t s, e;
   chunk_of(n, s, e);
-  double acc[1] = {0.0};
-  for (size_t t = s + threadIdx.x; t < e; t += kThreads) acc[0] = nanmax(acc[0], fabs((double)a[t]));
+  R m = R(0);
+  bool nan = false;
+  for (size_t t = s + threadIdx.x; t < e; t += kThreads) {
+    const R x = a[t];
+    nan |= (x != x);
+    const R ax = x < R(0) ? -x : x;
+    m = ax > m ? ax : m;
+  }
+  double acc[1] = {nan ? __longlong_as_double(0x7ff8000000000000ULL) : (double)m};
   double r[1];
   block_reduce<1, true>(acc, r);
   if (threadIdx.x == 0) part[blockIdx.x] = r[0];
@@ -88,13 +128,25 @@ __global__ void __launch_bounds__(kThreads) k_multidot_partial(const R* __restri
   const int i0 = blockIdx.y * 8;
   const int nv = min(8, m - i0);
   double acc[8];
+  if (sizeof(R) == 4) {
+    F2 f[8];
+    for (size_t t = s + threadIdx.x; t < e; t += kThreads) {
+      const float wt = (float)w[t];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-  for (size_t t = s + threadIdx.x; t < e; t += kThreads) {
-    const double wt = (double)w[t];
+      for (int i = 0; i < 8; ++i)
+        if (i < nv) f[i].add_product((float)V[(size_t)(i0 + i) * ldv + t], wt);
+    }
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i < nv) acc[i] += (double)V[(size_t)(i0 + i) * ldv + t] * wt;
+    for (int i = 0; i < 8; ++i) acc[i] = f[i].value();
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (size_t t = s + threadIdx.x; t < e; t += kThreads) {
+      const double wt = (double)w[t];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < nv) acc[i] = fma((double)V[(size_t)(i0 + i) * ldv + t], wt, acc[i]);
+    }
   }
   double r[8];
   block_reduce<8, false>(acc, r);
@@ -120,25 +172,29 @@ __global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ part
   }
 }
 
+// Vector updates run in the vectors' own precision (coefficients rounded to it once).
 template <typename R>
-__global__ void k_lincomb(size_t n, int nvec, double c0, double c1, double c2, double c3, const R* x0, const R* x1,
-                          const R* x2, const R* x3, R* out) {
+__global__ void k_lincomb(size_t n, int nvec, R c0, R c1, R c2, R c3, const R* x0, const R* x1, const R* x2,
+                          const R* x3, R* out) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double r = c0 * (double)x0[t];
-    if (nvec > 1) r += c1 * (double)x1[t];
-    if (nvec > 2) r += c2 * (double)x2[t];
-    if (nvec > 3) r += c3 * (double)x3[t];
-    out[t] = (R)r;
+    R r = c0 * x0[t];
+    if (nvec > 1) r = fma(c1, x1[t], r);
+    if (nvec > 2) r = fma(c2, x2[t], r);
+    if (nvec > 3) r = fma(c3, x3[t], r);
+    out[t] = r;
   }
 }
 
 template <typename R>
 __global__ void k_subtract_basis(const R* __restrict__ V, size_t ldv, int m, const double* __restrict__ h, R* w,
                                  size_t n) {
+  __shared__ R hs[256];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = (R)h[i];
+  __syncthreads();
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double r = (double)w[t];
-    for (int i = 0; i < m; ++i) r -= h[i] * (double)V[(size_t)i * ldv + t];
-    w[t] = (R)r;
+    R r = w[t];
+    for (int i = 0; i < m; ++i) r = fma(-hs[i], V[(size_t)i * ldv + t], r);
+    w[t] = r;
   }
 }
 
@@ -225,8 +281,9 @@ int launch_multidot(const fv_grid_s* g, const R* V, size_t ldv, int m, const R* 
 template <typename R>
 int launch_lincomb(const fv_grid_s* g, size_t n, int nvec, const double* c, const R* const* x, R* out) {
   ProfScope ps(g, PROF_VECTOR);
-  k_lincomb<R><<<stream_grid(n), 256, 0, g->stream>>>(n, nvec, c[0], nvec > 1 ? c[1] : 0.0, nvec > 2 ? c[2] : 0.0,
-                                                       nvec > 3 ? c[3] : 0.0, x[0], nvec > 1 ? x[1] : x[0],
+  k_lincomb<R><<<stream_grid(n), 256, 0, g->stream>>>(n, nvec, (R)c[0], (R)(nvec > 1 ? c[1] : 0.0),
+                                                       (R)(nvec > 2 ? c[2] : 0.0), (R)(nvec > 3 ? c[3] : 0.0),
+                                                       x[0], nvec > 1 ? x[1] : x[0],
                                                        nvec > 2 ? x[2] : x[0], nvec > 3 ? x[3] : x[0], out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
@@ -235,6 +292,7 @@ int launch_lincomb(const fv_grid_s* g, size_t n, int nvec, const double* c, cons
 template <typename R>
 int launch_subtract_basis(const fv_grid_s* g, const R* V, size_t ldv, int m, const double* h, R* w, size_t n) {
   if (m <= 0) return FV_OK;
+  if (m > 256) return FV_EINVAL;
   ProfScope ps(g, PROF_VECTOR);
   k_subtract_basis<R><<<stream_grid(n), 256, 0, g->stream>>>(V, ldv, m, h, w, n);
   FV_CUDA(cudaGetLastError());

@@ -11,15 +11,16 @@
 namespace fv {
 namespace {
 
+// 32-bit offsets: the grid constructor guarantees 4 * nx * ny * nz < 2^31.
 template <typename R>
 struct Cell {
   int p[3];
-  size_t s[3];
-  size_t o;
+  int s[3];
+  int o;
 };
 
 template <typename R>
-__device__ __forceinline__ R ld(const R* __restrict__ a, size_t o) {
+__device__ __forceinline__ R ld(const R* __restrict__ a, int o) {
   return __ldg(a + o);
 }
 
@@ -32,11 +33,11 @@ __device__ __forceinline__ R ld(const R* __restrict__ a, size_t o) {
 // C-face times the C-velocity interpolated along d to the d-face; zero through a wall.
 template <typename R, int C>
 __device__ __forceinline__ void momentum_terms(const Geo<R>& g, const R* __restrict__ a, const R* __restrict__ b,
-                                               size_t N, const Cell<R>& c, R& conv, R& lap) {
+                                               int N, const Cell<R>& c, R& conv, R& lap) {
   const R* aC = a + C * N;
   const R* bC = b + C * N;
   const int pc = c.p[C], nc = g.n[C];
-  const size_t o = c.o, sC = c.s[C];
+  const int o = c.o, sC = c.s[C];
   const R aH = ld(aC, o), bH = ld(bC, o);
   const R aM = (pc >= 2) ? ld(aC, o - sC) : R(0);
   const R bM = (pc >= 2) ? ld(bC, o - sC) : R(0);
@@ -54,7 +55,7 @@ __device__ __forceinline__ void momentum_terms(const Geo<R>& g, const R* __restr
     const R* aD = a + D * N;
     const R* bD = b + D * N;
     const int pd = c.p[D], nd = g.n[D];
-    const size_t sD = c.s[D];
+    const int sD = c.s[D];
     R fLo = R(0), fHi = R(0), gLo, gHi;
     if (pd >= 1) {  // lower d-face is interior
       const R aDc = wlC * ld(aD, o - sC) + wrC * ld(aD, o);
@@ -68,7 +69,7 @@ __device__ __forceinline__ void momentum_terms(const Geo<R>& g, const R* __restr
       gLo = bH * g.idc[D][0];
     }
     if (pd + 1 <= nd - 1) {  // upper d-face is interior
-      const size_t oU = o + sD;
+      const int oU = o + sD;
       const R aDc = wlC * ld(aD, oU - sC) + wrC * ld(aD, oU);
       const R bDc = wlC * ld(bD, oU - sC) + wrC * ld(bD, oU);
       const R bCp = ld(bC, oU), aCp = ld(aC, oU);
@@ -89,10 +90,10 @@ __device__ __forceinline__ void momentum_terms(const Geo<R>& g, const R* __restr
 // x = 0 and 0 at x = 1 (Eq. 4), zero flux through the y and z walls (Eqs. 5-6).
 template <typename R>
 __device__ __forceinline__ void temperature_terms(const Geo<R>& g, const R* __restrict__ a, const R* __restrict__ b,
-                                                  size_t N, const Cell<R>& c, R T_hot, R& conv, R& lap) {
+                                                  int N, const Cell<R>& c, R T_hot, R& conv, R& lap) {
   const R* Ta = a + 3 * N;
   const R* Tb = b + 3 * N;
-  const size_t o = c.o;
+  const int o = c.o;
   const R TaH = ld(Ta, o), TbH = ld(Tb, o);
   conv = R(0);
   lap = R(0);
@@ -101,7 +102,7 @@ __device__ __forceinline__ void temperature_terms(const Geo<R>& g, const R* __re
     const R* aD = a + D * N;
     const R* bD = b + D * N;
     const int pd = c.p[D], nd = g.n[D];
-    const size_t sD = c.s[D];
+    const int sD = c.s[D];
     R fLo = R(0), fHi = R(0), gLo = R(0), gHi = R(0);
     if (pd >= 1) {
       const R Tam = ld(Ta, o - sD), Tbm = ld(Tb, o - sD);
@@ -112,7 +113,7 @@ __device__ __forceinline__ void temperature_terms(const Geo<R>& g, const R* __re
       gLo = (TbH - T_hot) * g.idc[0][0];
     }
     if (pd + 1 <= nd - 1) {
-      const size_t oU = o + sD;
+      const int oU = o + sD;
       const R Tap = ld(Ta, oU), Tbp = ld(Tb, oU);
       const R wl = g.wl[D][pd + 1], wr = g.wr[D][pd + 1];
       fHi = ld(aD, oU) * (wl * TbH + wr * Tbp) + ld(bD, oU) * (wl * TaH + wr * Tap);
@@ -136,16 +137,16 @@ __device__ __forceinline__ bool cell_of_thread(const Geo<R>& g, Cell<R>& c) {
   c.p[1] = j;
   c.p[2] = k;
   c.s[0] = 1;
-  c.s[1] = (size_t)g.n[0];
-  c.s[2] = (size_t)g.n[0] * g.n[1];
-  c.o = ((size_t)k * g.n[1] + j) * g.n[0] + i;
+  c.s[1] = g.n[0];
+  c.s[2] = g.n[0] * g.n[1];
+  c.o = (k * g.n[1] + j) * g.n[0] + i;
   return true;
 }
 
 // mode 0: residual  out = -S(q,q)/2 + Lap q (+ Dirichlet data) + Gr T_q e_z
 // mode 1: J.v       out = -S(q,v) + Lap v + Gr T_v e_z - sigma v
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_stencil(Geo<R> g, size_t N, R Gr, R invPr, R sigma,
+__global__ void __launch_bounds__(256) k_stencil(Geo<R> g, int N, R Gr, R invPr, R sigma,
                                                   const R* __restrict__ q, const R* __restrict__ v,
                                                   R* __restrict__ out) {
   Cell<R> c;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256) k_stencil(Geo<R> g, size_t N, R Gr, R inv
 
 // rhs = D vel:  sum_d (vel_d(face p+1) - vel_d(face p)) / width, wall fluxes zero
 template <typename R>
-__global__ void __launch_bounds__(256) k_divergence(Geo<R> g, size_t N, const R* __restrict__ vel,
+__global__ void __launch_bounds__(256) k_divergence(Geo<R> g, int N, const R* __restrict__ vel,
                                                      R* __restrict__ rhs) {
   Cell<R> c;
   if (!cell_of_thread(g, c)) return;
@@ -210,14 +211,14 @@ __global__ void __launch_bounds__(256) k_divergence(Geo<R> g, size_t N, const R*
 // faces; T gets no gradient.  Wall slots -> 0.  out may alias Y or w (each element is read, then written,
 // by the same thread).
 template <typename R>
-__global__ void __launch_bounds__(256) k_correct(Geo<R> g, size_t N, const R* Y, const R* __restrict__ phi,
+__global__ void __launch_bounds__(256) k_correct(Geo<R> g, int N, const R* Y, const R* __restrict__ phi,
                                                   R alpha, const R* v, R beta, const R* w, R gamma, R* out) {
   Cell<R> c;
   if (!cell_of_thread(g, c)) return;
   const R ph = ld(phi, c.o);
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
-    const size_t o = d * N + c.o;
+    const int o = d * N + c.o;
     R r;
     if (d < 3) {
       if (c.p[d] == 0) {
@@ -254,7 +255,7 @@ int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F) {
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_STENCIL);
-  k_stencil<R, 0><<<grid, block, 0, g->stream>>>(geo_of<R>(g), g->N, (R)Gr, (R)(1.0 / g->Pr), R(0), q, q, F);
+  k_stencil<R, 0><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, (R)Gr, (R)(1.0 / g->Pr), R(0), q, q, F);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -264,7 +265,7 @@ int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R*
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_STENCIL);
-  k_stencil<R, 1><<<grid, block, 0, g->stream>>>(geo_of<R>(g), g->N, (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
+  k_stencil<R, 1><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -274,7 +275,7 @@ int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs) {
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_DIVERGENCE);
-  k_divergence<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), g->N, vel, rhs);
+  k_divergence<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, vel, rhs);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -285,7 +286,7 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_CORRECT);
-  k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), g->N, Y, phi, (R)alpha, v, (R)beta, w, (R)gamma, out);
+  k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w, (R)gamma, out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
