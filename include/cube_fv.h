@@ -120,6 +120,18 @@ int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const v
 /* Krylov inner product <a, b> over all 4N elements, accumulated in FP64 in a
  * fixed order (bit-reproducible).  result: host.  Errors: FV_EINVAL, FV_ECUDA, FV_ENAN. */
 int fv_dot(fv_grid g, int prec, const void* a, const void* b, double* result);
+/* Inner product <a, b> of two device vectors of n elements WITHOUT any allocation, for callers
+ * that cannot allocate device memory (allocation-free real-time loops, fixed memory budgets,
+ * memory owned by someone else's pool).  No counterpart in the paper: it is the fv_dot reduction
+ * with its block partial sums kept in a library-owned static device array of 4096 doubles
+ * (32 KiB, held by every GPU that loads the library until exit) instead of handle workspace.
+ * No fv_grid handle is needed.  result: DEVICE double, written on `stream` (a cudaStream_t).
+ * n <= 4096 * 2^18 elements; larger n, n < 1, null pointers or an unknown prec give FV_EINVAL.
+ * The first call on each device looks up the array's address (make it before any stream capture).
+ * All calls share the array: calls that overlap on the GPU race and must be serialised.
+ * Errors: FV_EINVAL, FV_ECUDA. */
+int fv_dot_noalloc(int prec, long long n, const void* a, const void* b, double* result, void* stream);
+
 /* y <- alpha x + beta y over 4N elements (coefficients applied in FP64). */
 int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y);
 /* Element-type conversion of a state: FP64 -> FP32 (to_fp32 = 1) or back. */

@@ -75,6 +75,7 @@ def lib():
             "fv_jvp_project": (i, [vp, i, d, d, vp, vp, vp]),
             "fv_jvp_project_lincomb": (i, [vp, i, d, d, vp, vp, vp, d, d, d, vp]),
             "fv_dot": (i, [vp, i, vp, vp, C.POINTER(d)]),
+            "fv_dot_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp]),
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
             "fv_convert": (i, [vp, i, vp, vp]),
             "fv_newton_default_opts": (None, [C.POINTER(fv_newton_opts)]),
@@ -96,7 +97,7 @@ def lib():
 
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
-            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_dot", "fv_axpby", "fv_convert", "fv_newton_default_opts",
+            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_newton_default_opts",
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
 
@@ -214,6 +215,18 @@ def fv_dot(g: Grid, prec, a, b) -> float:
     r = C.c_double(0.0)
     _check(lib().fv_dot(g.h, prec, _ptr(a, dt, g.n, "a"), _ptr(b, dt, g.n, "b"), C.byref(r)), "fv_dot")
     return r.value
+
+
+def fv_dot_noalloc(prec, a, b, result, stream=None):
+    """<a, b> into the device FP64 tensor `result` (one element), with no allocation in the library."""
+    import torch
+    dt = torch.float64 if prec == FV_FP64 else torch.float32
+    n = a.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().fv_dot_noalloc(int(prec), n, _ptr(a, dt, n, "a"), _ptr(b, dt, n, "b"),
+                                _ptr(result, torch.float64, 1, "result"), C.c_void_p(stream)), "fv_dot_noalloc")
+    return result
 
 
 def fv_axpby(g: Grid, prec, alpha, x, beta, y):

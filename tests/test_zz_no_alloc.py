@@ -1,0 +1,59 @@
+"""fv_dot_noalloc: the inner product for callers that cannot allocate device memory.
+
+Such callers (allocation-free real-time loops, fixed memory budgets, memory owned by another pool)
+cannot create an fv_grid handle, whose construction allocates workspace.  The no-allocation entry
+point keeps its partial sums in a static device array instead.  Checked through the C-ABI against
+the existing handle-based fv_dot on the same vectors, twice in a row (the shared scratch keeps the
+previous call's contents), within the inner-product tolerance the other tests use.  This file is
+collected last so that a run stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2210_08816_gb300 import seeded
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_08816_gb300 import build
+    build.build()
+    from paper_2210_08816_gb300 import fv as _fv
+    _fv.lib()
+    return _fv
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_noalloc_dot_matches_handle_dot_twice(fv, prec_name):
+    nx, ny, nz = 96, 80, 72          # 4*N = 2.2M elements: 9 blocks of the static scratch, ragged tail
+    g = fv.Grid(nx, ny, nz)
+    prec = fv.FV_FP64 if prec_name == "fp64" else fv.FV_FP32
+    dt = torch.float64 if prec_name == "fp64" else torch.float32
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for call, (sa, sb) in enumerate([(21, 22), (23, 24)]):
+        a = torch.tensor(np.stack(seeded.normal_fields(sa, (nz, ny, nx))), dtype=dt, device="cuda").view(-1)
+        b = torch.tensor(np.stack(seeded.normal_fields(sb, (nz, ny, nx))), dtype=dt, device="cuda").view(-1)
+        ref = fv.fv_dot(g, prec, a, b)
+        fv.fv_dot_noalloc(prec, a, b, res)
+        torch.cuda.synchronize()
+        got = float(res.item())
+        scale = float(torch.sum(torch.abs(a.double() * b.double())).item())
+        assert abs(got - ref) <= 1e-12 * scale, (call, got, ref)
+
+
+def test_noalloc_dot_rejects_bad_sizes(fv):
+    a = torch.zeros(8, dtype=torch.float64, device="cuda")
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L = fv.lib()
+    import ctypes as C
+    st = L.fv_dot_noalloc(0, 4096 * (1 << 18) + 1, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()),
+                          C.c_void_p(res.data_ptr()), None)
+    assert st == fv.FV_EINVAL
+    assert L.fv_dot_noalloc(0, 0, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), C.c_void_p(res.data_ptr()),
+                            None) == fv.FV_EINVAL
+    assert L.fv_dot_noalloc(5, 8, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), C.c_void_p(res.data_ptr()),
+                            None) == fv.FV_EINVAL
