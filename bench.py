@@ -65,6 +65,7 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x, device):
+    """Slowest rank's time (a scalar, not a data-path collective)."""
     if ws == 1:
         return x
     import torch
@@ -72,6 +73,11 @@ def max_over_ranks(ws, x, device):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     td.all_reduce(t, op=td.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws, steps_per_rank, ms_max):
+    """Whole-job value: every rank's steps over the slowest rank's time (replicas, weak scaling)."""
+    return ws * steps_per_rank / (ms_max / 1e3)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -227,7 +233,7 @@ def gpu_arm(args, ws, rank, local):
     barrier(ws)
     ms = max_over_ranks(ws, ms, device)
     ms_step = ms / K
-    value = ws * K / (ms / 1e3)
+    value = job_throughput(ws, K, ms)
     launches = sum(c for _, c in prof.values())
 
     # roofline of the dominant kernel class

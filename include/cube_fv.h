@@ -177,8 +177,10 @@ int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_newton_opts* o
 
 /* ---------------------------------------------------------------- Arnoldi */
 typedef struct {
-    int precision;        /* FV_FP64, or FV_FP32 Krylov vectors with FP64 Hessenberg,
-                             Gram-Schmidt coefficients and inner products */
+    int precision;        /* FV_FP64, or FV_FP32: a phase with FP32 Krylov vectors and
+                             J.v + projection (FP64 Hessenberg, Gram-Schmidt coefficients and
+                             inner products) down to residual 1e-4, then FP64 cycles started
+                             from its Ritz vectors refine to tol */
     int m;                /* Krylov subspace dimension per cycle */
     double tol;           /* stop when every wanted Ritz pair has
                              ||A x - lam x|| <= tol |lam| (Arnoldi estimate) */
@@ -199,6 +201,8 @@ typedef struct {
     double lam_scaled_re[64], lam_scaled_im[64];   /* lam / sqrt(Gr): the paper's scaling */
     int degrees[256];     /* Chebyshev degree per restart */
     double seconds;
+    int restarts_low;     /* FV_FP32: restarts of the FP32 phase (included in restarts) */
+    long long matvecs_low;/* FV_FP32: J.v + projections of the FP32 phase (included in matvecs) */
 } fv_arnoldi_report;
 
 void fv_arnoldi_default_opts(fv_arnoldi_opts* o);

@@ -271,7 +271,7 @@ def chebyshev_filter(A, y0, d, c2, lam_ref, degree):
 
 
 def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=200, min_degree=10,
-                      guard=2, power_steps=30):
+                      guard=2, power_steps=30, project=None, refresh=None, seed=12345, trace=None):
     """Leading k eigenpairs (largest real part) of A by Chebyshev-preconditioned Arnoldi.
 
     Returns (lam, X, info): lam complex (k or k+1 values when a conjugate pair
@@ -280,8 +280,14 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
 
     The filter keeps `guard` Ritz values beyond the k wanted ones outside its
     ellipse, so that the k-th and (k+1)-th eigenvalues are not damped against
-    each other; convergence is tested on the k wanted ones only.
+    each other; convergence is tested on the k wanted ones only.  Each restart
+    vector gets a small random component (relative weight `refresh`, default
+    tol / 100, made divergence free by `project`): a mode that a restart
+    happened to lose comes back above round-off, while the noise floor it adds
+    stays below the tolerance.
     """
+    rng = np.random.default_rng(seed)
+    refresh = 0.01 * tol if refresh is None else refresh
     x = x0 / np.linalg.norm(x0)
     info = {"restarts": 0, "matvecs": 0, "degrees": []}
     nmv = [0]
@@ -339,6 +345,12 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
         for i in range(nw):
             yi = Y[:, i].real if theta[i].imag >= 0 else Y[:, i].imag
             z += yi / max(np.linalg.norm(yi), 1e-300)
+        if refresh > 0.0:
+            r = rng.standard_normal(x.size)
+            r = project(r) if project is not None else r
+            z += refresh * np.linalg.norm(z) * r / np.linalg.norm(r)
+        if trace is not None:
+            trace(it, theta[:nw], est, d, c2, rate, deg)
         x = chebyshev_filter(Af, z, d, c2, lam_ref, deg)
         x = x / np.linalg.norm(x)
     raise AssertionError("unreachable")
@@ -373,5 +385,6 @@ def leading_eigenvalues(grid: Grid, Gr: float, q, k=4, m=20, seed_vector=None, t
     """Leading k eigenvalues of P J(q) on the divergence-free subspace (start vector projected)."""
     P = Projector(grid)
     A = shifted_operator(grid, Gr, q, default_shift(grid), P)
-    x0 = pack(P.full(unpack(grid, seed_vector)))
-    return chebyshev_arnoldi(A, x0, k=k, m=m, tol=tol, **kw)
+    proj = lambda x: pack(P.full(unpack(grid, x)))
+    x0 = proj(seed_vector)
+    return chebyshev_arnoldi(A, x0, k=k, m=m, tol=tol, project=proj, **kw)

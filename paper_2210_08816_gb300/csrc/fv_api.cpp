@@ -547,8 +547,16 @@ int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out) {
   }
   if (st == FV_OK) st = upload_axes<double>(g, ax, 0, g->geo64, g->fdm64);
   if (st == FV_OK) st = upload_axes<float>(g, ax, 1, g->geo32, g->fdm32);
+  if (st == FV_OK && tc_eligible(g)) {
+    std::vector<double> Einv[3] = {ax[0].Einv, ax[1].Einv, ax[2].Einv}, E[3] = {ax[0].E, ax[1].E, ax[2].E};
+    if (tc_setup(g, Einv, E) != FV_OK) {  // keep the SIMT passes
+      g->tc.ready = false;
+      cudaGetLastError();
+    }
+  }
   if (st == FV_OK) {
-    if (cudaMalloc(&g->ws.partials, sizeof(double) * kReduceBlocks * 256) != cudaSuccess ||
+    if (cudaMalloc(&g->ws.err, sizeof(int)) != cudaSuccess || cudaMemset(g->ws.err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&g->ws.partials, sizeof(double) * kReduceBlocks * 256) != cudaSuccess ||
         cudaMalloc(&g->ws.scalars, sizeof(double) * kMaxScalars) != cudaSuccess ||
         cudaMallocHost(&g->ws.host_scalars, sizeof(double) * kMaxScalars) != cudaSuccess) {
       cudaGetLastError();
@@ -579,6 +587,8 @@ int fv_grid_destroy(fv_grid g) {
   if (g->ws.scalars) cudaFree(g->ws.scalars);
   if (g->ws.host_scalars) cudaFreeHost(g->ws.host_scalars);
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  if (g->tc.buf) cudaFree(g->tc.buf);
+  if (g->ws.err) cudaFree(g->ws.err);
   delete g;
   return FV_OK;
 }
@@ -883,7 +893,8 @@ static void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz
 
 template <typename R>
 static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
-                        double* im, void* vecs_out, fv_arnoldi_report* rep) {
+                        double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start = nullptr,
+                        double* lam_far_io = nullptr) {
   const auto t_start = std::chrono::steady_clock::now();
   const size_t n = 4 * g->N;
   const int m = o.m;
@@ -904,12 +915,16 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   Operator<R> A{g, Gr, sigma, q, &mv};
   // start vector: seeded N(0,1), projected, normalised
   R* x = y0.p;
-  FV_TRY(launch_fill_normal<R>(g, o.seed, x));
+  if (start) {
+    FV_TRY(V.copy(x, start));
+  } else {
+    FV_TRY(launch_fill_normal<R>(g, o.seed, x));
+  }
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
   // far end of the spectrum: Rayleigh quotient of a short power iteration (filtered restarts stop
   // showing it, and the Chebyshev polynomial grows fast outside its ellipse)
-  double lam_far = 0.0;
-  {
+  double lam_far = (lam_far_io && *lam_far_io != 0.0) ? *lam_far_io : 0.0;
+  if (lam_far == 0.0) {
     R* z = y1.p;
     double zn2;
     FV_TRY(V.dot(x, x, &zn2));
@@ -921,6 +936,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       FV_TRY(V.dot(w.p, w.p, &wn2));
       FV_TRY(V.lin(z, {{1.0 / std::sqrt(wn2), w.p}}));
     }
+    if (lam_far_io) *lam_far_io = lam_far;
   }
   std::vector<double> H((size_t)(m + 1) * m), h(m + 1), hre, him, ycoef;
   std::vector<std::vector<double>> Y;
@@ -1114,6 +1130,17 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     FV_TRY(V.zero(z));
     FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, z, n));
     FV_CUDA(cudaStreamSynchronize(g->stream));
+    // a small divergence-free random component (relative weight tol / 100): a mode that a restart happened
+    // to lose comes back above round-off, while the noise floor stays below the tolerance
+    {
+      double zn2, rn2;
+      FV_TRY(launch_fill_normal<R>(g, o.seed + 1000003ULL * (unsigned long long)(restart + 1), w.p));
+      FV_TRY(project_inplace<R>(g, w.p, 1, 0.0, nullptr, nullptr));
+      FV_TRY(V.dot(z, z, &zn2));
+      FV_TRY(V.dot(w.p, w.p, &rn2));
+      const double eps = 0.01 * o.tol * std::sqrt(zn2 / std::max(rn2, 1e-300));
+      FV_TRY(V.lin(z, {{1.0, z}, {eps, w.p}}));
+    }
     // three-term recurrence: y1 = tau1 (A - d) y0; y_{j+1} = 2 tau_{j+1} (A - d) y_j - c2 tau_j tau_{j+1} y_{j-1}
     const double s = lam_ref - d;
     double tau = 1.0 / s;
@@ -1155,6 +1182,59 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
 
 }  // namespace fv
 
+namespace fv {
+
+// Mixed precision: FP32 Krylov vectors and J.v + projection until the Ritz residuals reach 1e-4 (with FP32
+// matvecs the residual floor is ~ u_32 ||A|| / |lam|, far above 1e-6 for the small leading eigenvalues of
+// this stiff operator), then FP64 Chebyshev-Arnoldi cycles started from the sum of the FP32 Ritz vectors
+// refine the same pairs to the requested tolerance.
+static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const fv_arnoldi_opts& o, double* re,
+                         double* im, void* vecs_out, fv_arnoldi_report* rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t n = 4 * g->N;
+  DevBuf<float> X32;
+  DevBuf<double> z64, t64, X64;
+  FV_TRY(X32.alloc((size_t)(k + 2) * n));
+  fv_arnoldi_opts o1 = o;
+  o1.tol = std::max(o.tol, 1e-4);
+  o1.max_restarts = std::min(o.max_restarts, 100);
+  fv_arnoldi_report r1;
+  std::memset(&r1, 0, sizeof(r1));
+  double lam_far = 0.0;
+  int st1 = arnoldi_impl<float>(g, k, Gr, q, o1, re, im, X32.p, &r1, nullptr, &lam_far);
+  if (st1 != FV_OK && st1 != FV_ENOCONV) return st1;
+  FV_TRY(z64.alloc(n));
+  FV_TRY(t64.alloc(n));
+  Vec<double> V{g, n};
+  FV_TRY(V.zero(z64.p));
+  for (int i = 0; i < r1.nconv; ++i) {
+    FV_TRY(launch_convert(g, n, X32.p + (size_t)i * n, t64.p));
+    double t2;
+    FV_TRY(V.dot(t64.p, t64.p, &t2));
+    if (t2 > 0.0) FV_TRY(V.lin(z64.p, {{1.0, z64.p}, {1.0 / std::sqrt(t2), t64.p}}));
+  }
+  fv_arnoldi_report r2;
+  std::memset(&r2, 0, sizeof(r2));
+  if (vecs_out) FV_TRY(X64.alloc((size_t)(k + 1) * n));
+  fv_arnoldi_opts o2 = o;
+  o2.precision = FV_FP64;
+  const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &lam_far);
+  if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
+    for (int i = 0; i < r2.nconv; ++i)
+      FV_TRY(launch_convert(g, n, X64.p + (size_t)i * n, (float*)vecs_out + (size_t)i * n));
+  *rep = r2;
+  rep->restarts_low = r1.restarts;
+  rep->matvecs_low = r1.matvecs;
+  rep->restarts = r1.restarts + r2.restarts;
+  rep->matvecs = r1.matvecs + r2.matvecs;
+  for (int i = 0; i < 256; ++i) rep->degrees[i] = (i <= r1.restarts) ? r1.degrees[i] : r2.degrees[i - r1.restarts - 1];
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+}  // namespace fv
+
 extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, const fv_arnoldi_opts* opts, double* re,
                                double* im, void* vecs, fv_arnoldi_report* report) {
   if (!g || !q || !re || !im) return invalid("null argument");
@@ -1169,8 +1249,12 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   fv_arnoldi_report rep;
   std::memset(&rep, 0, sizeof(rep));
-  const int st = (o.precision == FV_FP64) ? arnoldi_impl<double>(g, k, Gr, q, o, re, im, vecs, &rep)
-                                          : arnoldi_impl<float>(g, k, Gr, q, o, re, im, vecs, &rep);
+  int st;
+  if (o.precision == FV_FP64) {
+    st = arnoldi_impl<double>(g, k, Gr, q, o, re, im, vecs, &rep);
+  } else {
+    st = arnoldi_mixed(g, k, Gr, q, o, re, im, vecs, &rep);
+  }
   rep.status = st;
   if (report) *report = rep;
   return st;

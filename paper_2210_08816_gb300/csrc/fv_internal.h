@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -41,6 +42,7 @@ struct Workspace {
   void* Y[2] = {nullptr, nullptr};
   void* t0[2] = {nullptr, nullptr};
   void* t1[2] = {nullptr, nullptr};
+  int* err = nullptr;              // device error word of bounded device-side waits (0 = none)
   double* partials = nullptr;      // reduction partials
   double* scalars = nullptr;       // device scalars (reduction results)
   double* host_scalars = nullptr;  // pinned host mirror
@@ -58,6 +60,12 @@ struct Profiler {
   std::vector<ProfRecord> records;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
+};
+// Tensor-core (tcgen05) pressure-solve operands: per axis [fwd_hi, fwd_lo, bwd_hi, bwd_lo] tensor maps.
+struct TcState {
+  bool ready = false;
+  void* buf = nullptr;
+  CUtensorMap B[3][4];
 };
 }  // namespace fv
 
@@ -77,6 +85,7 @@ struct fv_grid_s {
   double sigma_default;
   double min_width[3];
   mutable fv::Profiler prof;
+  fv::TcState tc;
 };
 
 namespace fv {
@@ -145,6 +154,16 @@ constexpr int kMaxScalars = 512;
 
 // host scalar readback: copies `count` scalars starting at `slot` and synchronises
 int read_scalars(const fv_grid_s* g, int slot, int count, double* out);
+
+// Tiled TMA descriptor of a dense row-major tensor (kernels_tc.cu): rank <= 5, dims innermost first,
+// strides in bytes for dims 1..rank-1, zero fill out of bounds.  FV_ECUDA if the driver call fails.
+int encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* ptr, const uint64_t* dims,
+                      const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swizzle);
+
+// Tensor-core pressure-solve passes (kernels_tc.cu), FP32 only.
+bool tc_eligible(const fv_grid_s* g);
+int tc_setup(fv_grid_s* g, const std::vector<double>* Einv, const std::vector<double>* E);
+int tc_pass(const fv_grid_s* g, int axis, int which, int na, int nb, const float* in, float* out, bool scale);
 
 // ------------------------------------------------------------------ host linear algebra (host_linalg.cpp)
 // Symmetric tridiagonal eigen-decomposition (implicit QR with Wilkinson shifts).

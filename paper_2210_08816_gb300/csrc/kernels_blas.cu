@@ -9,6 +9,8 @@
 // compensated pair (hi, lo) of floats: the product a*b is split exactly into p + e with an FMA and added
 // by Knuth's TwoSum, so a thread's partial carries ~44 significant bits before it is converted to FP64.
 // This keeps the inner products at FP64-like accuracy on GB300, whose FP64 pipe is ~1/64 of FP32.
+#include <string>
+
 #include "fv_internal.h"
 
 namespace fv {
@@ -323,7 +325,14 @@ int launch_fill_normal(const fv_grid_s* g, unsigned long long seed, R* out) {
 int read_scalars(const fv_grid_s* g, int slot, int count, double* out) {
   FV_CUDA(cudaMemcpyAsync(g->ws.host_scalars, g->ws.scalars + slot, sizeof(double) * count, cudaMemcpyDeviceToHost,
                           g->stream));
+  int dev_err = 0;
+  if (g->ws.err) FV_CUDA(cudaMemcpyAsync(&dev_err, g->ws.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   FV_CUDA(cudaStreamSynchronize(g->stream));
+  if (dev_err != 0) {
+    cudaMemsetAsync(g->ws.err, 0, sizeof(int), g->stream);
+    set_error("a bounded device-side wait expired (code " + std::to_string(dev_err) + ")");
+    return FV_ETIMEOUT;
+  }
   for (int i = 0; i < count; ++i) out[i] = g->ws.host_scalars[i];
   return FV_OK;
 }

@@ -4,14 +4,15 @@
 // S symmetric tridiagonal).  With the generalised eigenvectors E (E^T W E = I) and eigenvalues lam,
 //     phi = (E_z x E_y x E_x) diag(1 / (lam_x + lam_y + lam_z)) (E_z x E_y x E_x)^-1 rhs,
 // the constant mode (all three lam = 0) set to zero.  Each factor is a dense n x n matrix applied along
-// one axis: a batched GEMM with K = n.  Six passes: x, y, z forward (the z pass scales by 1/Lambda in
-// its epilogue), z, y, x backward.
+// one axis: a batched GEMM with K = n.
 //
-// Transform kernel: C[b][r][c] = sum_k A[b][r][k] B[b][k][c] with A k-contiguous in both layouts used:
-//   layout X (contract the contiguous x axis): rows = (k, j) lines, cols = modes, A = field, B(k, c) = M[c][k]
-//   layout S (contract a strided axis):         rows = modes, cols = contiguous positions, A = M, B = field
-// Tiles BM x BN, slabs of BK, 256 threads; thread (tx, ty) owns rows ty + 16 i and cols tx + 16 j so
-// that each store instruction writes 16 consecutive elements.
+// Rotating passes.  Every pass contracts the CONTIGUOUS axis of its input and writes the mode index as
+// the new slowest axis:  in[a][b][k] (k contiguous)  ->  out[m][a][b] = sum_k M[m][k] in[a][b][k].
+// Three passes turn (z, y, x) into (x, z, y), (y, x, z) and back to (z, y, x); the forward three map
+// cells to modes (the third one divides by Lambda in its epilogue), the backward three map back.  So
+// all six are one GEMM shape, C[p][m] = sum_k A[p][k] B[m][k] with both operands k-contiguous, stored
+// transposed (out[m][p]).  Tiles BM (p) x BN (m), slabs of BK; thread (tx, ty) owns p = tx + 16 i and
+// m = ty + 16 j, so each store instruction writes 16 consecutive p.
 #include "fv_internal.h"
 
 namespace fv {
@@ -21,26 +22,22 @@ template <typename R>
 struct TileCfg;
 template <>
 struct TileCfg<float> {
-  static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8;
+  static constexpr int BM = 128, BN = 128, BK = 32, TM = 8, TN = 8;
 };
 template <>
 struct TileCfg<double> {
   static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
 };
 
-struct TransformArgs {
-  int rows, cols, K;
-  long long lda_r;            // A: k stride is 1
-  long long ldb_k, ldb_c;     // B strides
-  long long ldc_r;            // C: col stride is 1
-  long long batch_a, batch_b, batch_c;
-  // scaling epilogue (z-forward): value /= (lz[r] + ly[c / nxm] + lx[c % nxm]); constant mode -> 0
-  int scale, nxm;
+struct PassArgs {
+  int P, nm, K;          // rows (a*b), modes, contraction length
+  int scale;             // third forward pass: divide by lam_z[m] + lam_y[p / nb] + lam_x[p % nb]
+  int nb;
 };
 
-template <typename R, bool B_COLS_CONTIG>
-__global__ void __launch_bounds__(256) k_transform(TransformArgs t, const R* __restrict__ A, const R* __restrict__ B,
-                                                    R* __restrict__ Cout, const R* __restrict__ lx,
+template <typename R>
+__global__ void __launch_bounds__(256) k_transform(PassArgs t, const R* __restrict__ in, const R* __restrict__ M,
+                                                    R* __restrict__ out, const R* __restrict__ lx,
                                                     const R* __restrict__ ly, const R* __restrict__ lz) {
   using T = TileCfg<R>;
   constexpr int BM = T::BM, BN = T::BN, BK = T::BK, TM = T::TM, TN = T::TN;
@@ -48,11 +45,7 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs t, const R* __r
   __shared__ R Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-  const long long bz = blockIdx.z;
-  A += bz * t.batch_a;
-  B += bz * t.batch_b;
-  Cout += bz * t.batch_c;
+  const int p0 = blockIdx.x * BM, m0 = blockIdx.y * BN;
   R acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -60,37 +53,26 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs t, const R* __r
     for (int j = 0; j < TN; ++j) acc[i][j] = R(0);
 
   for (int k0 = 0; k0 < t.K; k0 += BK) {
-    // A tile: BM x BK, k fastest
 #pragma unroll
     for (int e = tid; e < BM * BK; e += 256) {
       const int kk = e % BK, rr = e / BK;
-      const int r = r0 + rr, k = k0 + kk;
-      As[kk][rr] = (r < t.rows && k < t.K) ? A[(long long)r * t.lda_r + k] : R(0);
+      const int p = p0 + rr, k = k0 + kk;
+      As[kk][rr] = (p < t.P && k < t.K) ? in[(long long)p * t.K + k] : R(0);
     }
-    // B tile: BK x BN
-    if (B_COLS_CONTIG) {
 #pragma unroll
-      for (int e = tid; e < BN * BK; e += 256) {
-        const int cc = e % BN, kk = e / BN;
-        const int c = c0 + cc, k = k0 + kk;
-        Bs[kk][cc] = (c < t.cols && k < t.K) ? B[(long long)k * t.ldb_k + c] : R(0);
-      }
-    } else {
-#pragma unroll
-      for (int e = tid; e < BN * BK; e += 256) {
-        const int kk = e % BK, cc = e / BK;
-        const int c = c0 + cc, k = k0 + kk;
-        Bs[kk][cc] = (c < t.cols && k < t.K) ? B[(long long)c * t.ldb_c + k] : R(0);
-      }
+    for (int e = tid; e < BN * BK; e += 256) {
+      const int kk = e % BK, cc = e / BK;
+      const int m = m0 + cc, k = k0 + kk;
+      Bs[kk][cc] = (m < t.nm && k < t.K) ? M[(long long)m * t.K + k] : R(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       R a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -99,20 +81,19 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs t, const R* __r
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= t.rows) continue;
+  for (int j = 0; j < TN; ++j) {
+    const int m = m0 + ty + 16 * j;
+    if (m >= t.nm) continue;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int c = c0 + tx + 16 * j;
-      if (c >= t.cols) continue;
+    for (int i = 0; i < TM; ++i) {
+      const int p = p0 + tx + 16 * i;
+      if (p >= t.P) continue;
       R val = acc[i][j];
       if (t.scale) {
-        const int my = c / t.nxm, mx = c - my * t.nxm;
-        const R den = lz[r] + ly[my] + lx[mx];
-        val = (r == 0 && my == 0 && mx == 0) ? R(0) : val / den;
+        const int a = p / t.nb, b = p - a * t.nb;
+        val = (m == 0 && a == 0 && b == 0) ? R(0) : val / (lz[m] + ly[a] + lx[b]);
       }
-      Cout[(long long)r * t.ldc_r + c] = val;
+      out[(long long)m * t.P + p] = val;
     }
   }
 }
@@ -124,62 +105,20 @@ const FdmDev<double>& fdm_of<double>(const fv_grid_s* g) { return g->fdm64; }
 template <>
 const FdmDev<float>& fdm_of<float>(const fv_grid_s* g) { return g->fdm32; }
 
-// contract the x axis: out[(k,j)][m] = sum_i in[(k,j)][i] M[m][i]
+// in[a][b][k] -> out[m][a][b] with M (nm x K)
 template <typename R>
-int apply_x(const fv_grid_s* g, const R* M, const R* in, R* out) {
-  using T = TileCfg<R>;
-  TransformArgs t{};
-  t.rows = g->ny * g->nz;
-  t.cols = g->nx;
-  t.K = g->nx;
-  t.lda_r = g->nx;
-  t.ldb_k = 1;
-  t.ldb_c = g->nx;
-  t.ldc_r = g->nx;
-  dim3 grid((t.cols + T::BN - 1) / T::BN, (t.rows + T::BM - 1) / T::BM, 1);
-  ProfScope ps(g, PROF_TRANSFORM);
-  k_transform<R, false><<<grid, 256, 0, g->stream>>>(t, in, M, out, nullptr, nullptr, nullptr);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
-}
-
-// contract the y axis (batched over k-planes): out[k][m][i] = sum_j M[m][j] in[k][j][i]
-template <typename R>
-int apply_y(const fv_grid_s* g, const R* M, const R* in, R* out) {
-  using T = TileCfg<R>;
-  TransformArgs t{};
-  t.rows = g->ny;
-  t.cols = g->nx;
-  t.K = g->ny;
-  t.lda_r = g->ny;
-  t.ldb_k = g->nx;
-  t.ldc_r = g->nx;
-  t.batch_a = 0;
-  t.batch_b = t.batch_c = (long long)g->nx * g->ny;
-  dim3 grid((t.cols + T::BN - 1) / T::BN, (t.rows + T::BM - 1) / T::BM, g->nz);
-  ProfScope ps(g, PROF_TRANSFORM);
-  k_transform<R, true><<<grid, 256, 0, g->stream>>>(t, M, in, out, nullptr, nullptr, nullptr);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
-}
-
-// contract the z axis: out[m][(j,i)] = sum_k M[m][k] in[k][(j,i)], optionally scaled by 1/Lambda
-template <typename R>
-int apply_z(const fv_grid_s* g, const R* M, const R* in, R* out, bool scale) {
+int pass(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale) {
   using T = TileCfg<R>;
   const FdmDev<R>& f = fdm_of<R>(g);
-  TransformArgs t{};
-  t.rows = g->nz;
-  t.cols = g->nx * g->ny;
-  t.K = g->nz;
-  t.lda_r = g->nz;
-  t.ldb_k = (long long)g->nx * g->ny;
-  t.ldc_r = (long long)g->nx * g->ny;
+  PassArgs t{};
+  t.P = na * nb;
+  t.nm = K;
+  t.K = K;
   t.scale = scale ? 1 : 0;
-  t.nxm = g->nx;
-  dim3 grid((t.cols + T::BN - 1) / T::BN, (t.rows + T::BM - 1) / T::BM, 1);
+  t.nb = nb;
+  dim3 grid((t.P + T::BM - 1) / T::BM, (t.nm + T::BN - 1) / T::BN, 1);
   ProfScope ps(g, PROF_TRANSFORM);
-  k_transform<R, true><<<grid, 256, 0, g->stream>>>(t, M, in, out, f.lam[0], f.lam[1], f.lam[2]);
+  k_transform<R><<<grid, 256, 0, g->stream>>>(t, in, M, out, f.lam[0], f.lam[1], f.lam[2]);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -189,17 +128,40 @@ int apply_z(const fv_grid_s* g, const R* M, const R* in, R* out, bool scale) {
 template <typename R>
 int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp) {
   const FdmDev<R>& f = fdm_of<R>(g);
-  // rhs -> tmp -> phi -> tmp (scaled) -> phi -> tmp -> phi
-  FV_TRY(apply_x<R>(g, f.Einv[0], rhs, tmp));
-  FV_TRY(apply_y<R>(g, f.Einv[1], tmp, phi));
-  FV_TRY(apply_z<R>(g, f.Einv[2], phi, tmp, true));
-  FV_TRY(apply_z<R>(g, f.E[2], tmp, phi, false));
-  FV_TRY(apply_y<R>(g, f.E[1], phi, tmp));
-  FV_TRY(apply_x<R>(g, f.E[0], tmp, phi));
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  // forward: (z,y,x) -> (mx,z,y) -> (my,mx,z) -> (mz,my,mx) / Lambda
+  FV_TRY(pass<R>(g, f.Einv[0], nz, ny, nx, rhs, tmp, false));
+  FV_TRY(pass<R>(g, f.Einv[1], nx, nz, ny, tmp, phi, false));
+  FV_TRY(pass<R>(g, f.Einv[2], ny, nx, nz, phi, tmp, true));
+  // backward: (mz,my,mx) -> (x,mz,my) -> (y,x,mz) -> (z,y,x)
+  FV_TRY(pass<R>(g, f.E[0], nz, ny, nx, tmp, phi, false));
+  FV_TRY(pass<R>(g, f.E[1], nx, nz, ny, phi, tmp, false));
+  FV_TRY(pass<R>(g, f.E[2], ny, nx, nz, tmp, phi, false));
+  return FV_OK;
+}
+
+template <>
+int launch_poisson<float>(const fv_grid_s* g, const float* rhs, float* phi, float* tmp) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  if (g->tc.ready) {  // the same six passes on the tensor cores (3 x TF32 split, FP32 accuracy)
+    FV_TRY(tc_pass(g, 0, 0, nz, ny, rhs, tmp, false));
+    FV_TRY(tc_pass(g, 1, 0, nx, nz, tmp, phi, false));
+    FV_TRY(tc_pass(g, 2, 0, ny, nx, phi, tmp, true));
+    FV_TRY(tc_pass(g, 0, 2, nz, ny, tmp, phi, false));
+    FV_TRY(tc_pass(g, 1, 2, nx, nz, phi, tmp, false));
+    FV_TRY(tc_pass(g, 2, 2, ny, nx, tmp, phi, false));
+    return FV_OK;
+  }
+  const FdmDev<float>& f = fdm_of<float>(g);
+  FV_TRY(pass<float>(g, f.Einv[0], nz, ny, nx, rhs, tmp, false));
+  FV_TRY(pass<float>(g, f.Einv[1], nx, nz, ny, tmp, phi, false));
+  FV_TRY(pass<float>(g, f.Einv[2], ny, nx, nz, phi, tmp, true));
+  FV_TRY(pass<float>(g, f.E[0], nz, ny, nx, tmp, phi, false));
+  FV_TRY(pass<float>(g, f.E[1], nx, nz, ny, phi, tmp, false));
+  FV_TRY(pass<float>(g, f.E[2], ny, nx, nz, tmp, phi, false));
   return FV_OK;
 }
 
 template int launch_poisson<double>(const fv_grid_s*, const double*, double*, double*);
-template int launch_poisson<float>(const fv_grid_s*, const float*, float*, float*);
 
 }  // namespace fv

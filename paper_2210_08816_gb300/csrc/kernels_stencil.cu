@@ -6,6 +6,8 @@
 // x-face u at x_f[i], the y-face v at y_f[j], the z-face w at z_f[k] and T at the centre.
 // Wall slots (i == 0 for u, ...) are written as zero.  Inputs are read through the read-only
 // path; the neighbour re-reads of a block are served by L1/L2, so DRAM sees each field ~once.
+#include <cstring>
+
 #include "fv_internal.h"
 
 namespace fv {
@@ -190,6 +192,283 @@ __global__ void __launch_bounds__(256) k_stencil(Geo<R> g, int N, R Gr, R invPr,
   out[3 * N + c.o] = r;
 }
 
+// ------------------------------------------------------------------------------------------------
+// z-marching variant.  A block owns a 32 x 8 (x, y) tile of cells and marches over a chunk of kZChunk
+// planes.  For every input array it keeps the planes k-1, k, k+1 of the tile plus a one-cell x/y halo in
+// a 4-slot shared-memory ring (slot = plane mod 4); cp.async copies of plane k+2 fly while plane k is
+// computed.  Each input element is read from global memory ~1.3 times (halo) instead of ~7 times
+// through L1 as in the one-thread-per-cell kernel.
+// Plane tile of one array in shared memory: kHY rows of kPW elements; the cell (tx, ty) sits at row ty + 1,
+// column tx + kX0 (columns kX0 - 1 .. kX0 + kTX hold the x halo; the TMA box starts 4 columns left of the
+// tile so that its x coordinate stays on a 16-byte boundary).
+constexpr int kTX = 32, kTY = 8, kHY = kTY + 2, kPW = 40, kX0 = 4, kPL = kHY * kPW, kZChunk = 32;
+
+template <typename R, int NA>
+struct Ring {
+  const R* p[3];  // per dz in {-1, 0, +1}: this thread's cell in array 0's slot of that plane
+  // array a sits a * kPL further on within a plane slot (a, dx, dy, dz are compile-time constants)
+  __device__ __forceinline__ R at(int a, int dx, int dy, int dz) const {
+    return p[dz + 1][a * kPL + dy * kPW + dx];
+  }
+};
+
+__host__ __device__ constexpr int unit(int d, int c) { return d == c ? 1 : 0; }
+
+// Same mathematics as momentum_terms / temperature_terms, reading neighbours from the ring.
+// Arrays 0..3 are the advecting state a, arrays AB..AB+3 the advected field b (AB = 0 for F, 4 for J.v).
+template <typename R, int C, int NA, int AB>
+__device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], R& conv, R& lap) {
+  constexpr int cx = unit(C, 0), cy = unit(C, 1), cz = unit(C, 2);
+  const int pc = p[C], nc = g.n[C];
+  const R aH = S.at(C, 0, 0, 0), bH = S.at(AB + C, 0, 0, 0);
+  const R aM = (pc >= 2) ? S.at(C, -cx, -cy, -cz) : R(0);
+  const R bM = (pc >= 2) ? S.at(AB + C, -cx, -cy, -cz) : R(0);
+  const R aP = (pc + 1 < nc) ? S.at(C, cx, cy, cz) : R(0);
+  const R bP = (pc + 1 < nc) ? S.at(AB + C, cx, cy, cz) : R(0);
+  const R idcC = g.idc[C][pc];
+  const R aE = R(0.5) * (aH + aP), bE = R(0.5) * (bH + bP);
+  const R aW = R(0.5) * (aM + aH), bW = R(0.5) * (bM + bH);
+  conv = R(2) * (aE * bE - aW * bW) * idcC;
+  lap = ((bP - bH) * g.idx[C][pc] - (bH - bM) * g.idx[C][pc - 1]) * idcC;
+  const R wlC = g.wl[C][pc], wrC = g.wr[C][pc];
+#pragma unroll
+  for (int t = 1; t <= 2; ++t) {
+    const int D = (C + t) % 3;
+    const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
+    const int pd = p[D], nd = g.n[D];
+    R fLo = R(0), fHi = R(0), gLo, gHi;
+    if (pd >= 1) {
+      const R aDc = wlC * S.at(D, -cx, -cy, -cz) + wrC * S.at(D, 0, 0, 0);
+      const R bDc = wlC * S.at(AB + D, -cx, -cy, -cz) + wrC * S.at(AB + D, 0, 0, 0);
+      const R bCm = S.at(AB + C, -dx, -dy, -dz), aCm = S.at(C, -dx, -dy, -dz);
+      const R aCd = g.wl[D][pd] * aCm + g.wr[D][pd] * aH;
+      const R bCd = g.wl[D][pd] * bCm + g.wr[D][pd] * bH;
+      fLo = aDc * bCd + bDc * aCd;
+      gLo = (bH - bCm) * g.idc[D][pd];
+    } else {
+      gLo = bH * g.idc[D][0];
+    }
+    if (pd + 1 <= nd - 1) {
+      const R aDc = wlC * S.at(D, dx - cx, dy - cy, dz - cz) + wrC * S.at(D, dx, dy, dz);
+      const R bDc = wlC * S.at(AB + D, dx - cx, dy - cy, dz - cz) + wrC * S.at(AB + D, dx, dy, dz);
+      const R bCp = S.at(AB + C, dx, dy, dz), aCp = S.at(C, dx, dy, dz);
+      const R aCd = g.wl[D][pd + 1] * aH + g.wr[D][pd + 1] * aCp;
+      const R bCd = g.wl[D][pd + 1] * bH + g.wr[D][pd + 1] * bCp;
+      fHi = aDc * bCd + bDc * aCd;
+      gHi = (bCp - bH) * g.idc[D][pd + 1];
+    } else {
+      gHi = -bH * g.idc[D][nd];
+    }
+    const R ixD = g.idx[D][pd];
+    conv += (fHi - fLo) * ixD;
+    lap += (gHi - gLo) * ixD;
+  }
+}
+
+template <typename R, int NA, int AB>
+__device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], R T_hot,
+                                                 R& conv, R& lap) {
+  const R TaH = S.at(3, 0, 0, 0), TbH = S.at(AB + 3, 0, 0, 0);
+  conv = R(0);
+  lap = R(0);
+#pragma unroll
+  for (int D = 0; D < 3; ++D) {
+    const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
+    const int pd = p[D], nd = g.n[D];
+    R fLo = R(0), fHi = R(0), gLo = R(0), gHi = R(0);
+    if (pd >= 1) {
+      const R Tam = S.at(3, -dx, -dy, -dz), Tbm = S.at(AB + 3, -dx, -dy, -dz);
+      const R wl = g.wl[D][pd], wr = g.wr[D][pd];
+      fLo = S.at(D, 0, 0, 0) * (wl * Tbm + wr * TbH) + S.at(AB + D, 0, 0, 0) * (wl * Tam + wr * TaH);
+      gLo = (TbH - Tbm) * g.idc[D][pd];
+    } else if (D == 0) {
+      gLo = (TbH - T_hot) * g.idc[0][0];
+    }
+    if (pd + 1 <= nd - 1) {
+      const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
+      const R wl = g.wl[D][pd + 1], wr = g.wr[D][pd + 1];
+      fHi = S.at(D, dx, dy, dz) * (wl * TbH + wr * Tbp) + S.at(AB + D, dx, dy, dz) * (wl * TaH + wr * Tap);
+      gHi = (Tbp - TbH) * g.idc[D][pd + 1];
+    } else if (D == 0) {
+      gHi = -TbH * g.idc[0][nd];
+    }
+    const R ixD = g.idx[D][pd];
+    conv += (fHi - fLo) * ixD;
+    lap += (gHi - gLo) * ixD;
+  }
+}
+
+// cp.async copy of one element (4 or 8 bytes); src_bytes = 0 fills the destination with zero (halo outside
+// the box)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int src_bytes) {
+  static_assert(BYTES == 4 || BYTES == 8, "element size");
+  if (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kRing = 4;  // planes k-1, k, k+1 in use, k+2 in flight
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on an mbarrier phase; on expiry records code 16 in *err
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (bar_try(bar, parity)) return true;
+  atomicCAS(err, 0, 16);
+  return false;
+}
+
+// MODE 0: residual (arrays: q), MODE 1: J.v (arrays: q then v).  use_tma: plane tiles arrive by one 4D TMA
+// box per state (x, y, z, field) with zero fill outside the domain; otherwise by per-element cp.async.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kTX * kTY, 3)
+    k_stencil_z(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int use_tma,
+                int* err, Geo<R> g, int N, R Gr, R invPr, R sigma, const R* __restrict__ q, const R* __restrict__ v,
+                R* __restrict__ out) {
+  constexpr int NA = (MODE == 0) ? 4 : 8;
+  constexpr int AB = (MODE == 0) ? 0 : 4;
+  constexpr int NWARP = kTX * kTY / 32;
+  constexpr uint32_t kBox = 4u * kPL * sizeof(R);  // one state's box: 4 fields x kHY x kPW
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[kRing];
+  R* sm = reinterpret_cast<R*>(smem_raw);  // [kRing][NA][kPL]
+  const int tid = threadIdx.x;
+  const int tx = tid % kTX, ty = tid / kTX;
+  const int warp = tid / 32, lane = tid % 32;
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kZChunk;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int kend = min(k0 + kZChunk, nz);
+  if (use_tma && tid == 0) {
+    for (int s = 0; s < kRing; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue_plane = [&](int kk) {
+    R* slot = sm + ((kk + kRing) % kRing) * NA * kPL;
+    const bool kin = (kk >= 0 && kk < nz);
+    if (use_tma) {
+      const uint32_t b = smem_addr(&bar[(kk + kRing) % kRing]);
+      if (kin) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kBox * (NA / 4))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
+              "%5, %6}], [%2];" ::"r"(smem_addr(slot)),
+              "l"(reinterpret_cast<uint64_t>(&tmq)), "r"(b), "r"(i0 - kX0), "r"(j0 - 1), "r"(kk), "r"(0)
+              : "memory");
+          if (NA == 8)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+                "%4, %5, %6}], [%2];" ::"r"(smem_addr(slot + 4 * kPL)),
+                "l"(reinterpret_cast<uint64_t>(&tmv)), "r"(b), "r"(i0 - kX0), "r"(j0 - 1), "r"(kk), "r"(0)
+                : "memory");
+        }
+      } else {  // a plane outside the domain: zeros, and a plain arrival completes the barrier phase
+        for (int e = tid; e < NA * kPL; e += kTX * kTY) slot[e] = R(0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+      }
+      return;
+    }
+    // warp w copies halo rows w, w + NWARP, ...; lane l copies columns l and 32 + l of the (kTX + 2) halo row
+    for (int row = warp; row < NA * kHY; row += NWARP) {
+      const int arr = row / kHY, hy = row - arr * kHY;
+      const int j = j0 + hy - 1;
+      const R* base = (arr < 4) ? q + arr * N : v + (arr - 4) * N;
+      const bool rin = kin && j >= 0 && j < ny;
+      const int roff = (kk * ny + j) * nx + i0 - 1;
+      for (int hx = lane; hx < kTX + 2; hx += 32) {
+        const int i = i0 + hx - 1;
+        const bool in = rin && i >= 0 && i < nx;
+        cp_async_elem<sizeof(R)>(slot + arr * kPL + hy * kPW + (kX0 - 1) + hx, in ? base + roff + hx : base,
+                                 in ? (int)sizeof(R) : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  // plane kk lives in slot kk mod kRing; it is that slot's use number (kk - k0 + 1) / kRing
+  auto wait_plane = [&](int kk) -> bool {
+    if (!use_tma) return true;
+    return bar_wait(smem_addr(&bar[(kk + kRing) % kRing]), (uint32_t)(((kk - k0 + 1) / kRing) & 1), err);
+  };
+  issue_plane(k0 - 1);
+  issue_plane(k0);
+  issue_plane(k0 + 1);
+  if (!use_tma) cp_async_wait_all();
+  __syncthreads();
+  bool ok = wait_plane(k0 - 1);
+  ok = wait_plane(k0) && ok;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = (i < nx && j < ny);
+  const R half = (MODE == 0) ? R(0.5) : R(1);
+  for (int k = k0; k < kend; ++k) {
+    if (k + 2 <= kend) issue_plane(k + 2);  // plane k+2 feeds the output plane k+1
+    const bool ready = wait_plane(k + 1) && ok;
+    if (active && ready) {
+      Ring<R, NA> S;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+        S.p[dz + 1] = sm + ((k + dz + kRing) % kRing) * NA * kPL + (ty + 1) * kPW + (tx + kX0);
+      const int p[3] = {i, j, k};
+      const int o = (k * ny + j) * nx + i;
+      R conv, lap;
+      if (i >= 1) {
+        momentum_ring<R, 0, NA, AB>(g, S, p, conv, lap);
+        R r = lap - half * conv;
+        if (MODE == 1) r -= sigma * S.at(AB + 0, 0, 0, 0);
+        out[o] = r;
+      } else {
+        out[o] = R(0);
+      }
+      if (j >= 1) {
+        momentum_ring<R, 1, NA, AB>(g, S, p, conv, lap);
+        R r = lap - half * conv;
+        if (MODE == 1) r -= sigma * S.at(AB + 1, 0, 0, 0);
+        out[N + o] = r;
+      } else {
+        out[N + o] = R(0);
+      }
+      if (k >= 1) {
+        momentum_ring<R, 2, NA, AB>(g, S, p, conv, lap);
+        const R Tf = g.wl[2][k] * S.at(AB + 3, 0, 0, -1) + g.wr[2][k] * S.at(AB + 3, 0, 0, 0);
+        R r = lap - half * conv + Gr * Tf;
+        if (MODE == 1) r -= sigma * S.at(AB + 2, 0, 0, 0);
+        out[2 * N + o] = r;
+      } else {
+        out[2 * N + o] = R(0);
+      }
+      temperature_ring<R, NA, AB>(g, S, p, (MODE == 0) ? R(1) : R(0), conv, lap);
+      R r = lap * invPr - half * conv;
+      if (MODE == 1) r -= sigma * S.at(AB + 3, 0, 0, 0);
+      out[3 * N + o] = r;
+    }
+    if (!use_tma) cp_async_wait_all();  // plane k+2 has landed
+    __syncthreads();                    // nobody reads the slot of plane k-1 any more
+  }
+}
+
 // rhs = D vel:  sum_d (vel_d(face p+1) - vel_d(face p)) / width, wall fluxes zero
 template <typename R>
 __global__ void __launch_bounds__(256) k_divergence(Geo<R> g, int N, const R* __restrict__ vel,
@@ -250,24 +529,49 @@ inline void cell_grid(const fv_grid_s* g, dim3& grid, dim3& block) {
 
 }  // namespace
 
+// 4D tensor map of one state (x, y, z, field) with boxes of kPW x kHY x 1 x 4 elements
 template <typename R>
-int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F) {
-  dim3 grid, block;
-  cell_grid(g, grid, block);
+int state_map(const fv_grid_s* g, const R* ptr, CUtensorMap* m) {
+  const size_t sz = sizeof(R);
+  const uint64_t dims[4] = {(uint64_t)g->nx, (uint64_t)g->ny, (uint64_t)g->nz, 4};
+  const uint64_t strides[3] = {g->nx * sz, (uint64_t)g->nx * g->ny * sz, g->N * sz};
+  const uint32_t box[4] = {(uint32_t)kPW, (uint32_t)kHY, 1, 4};
+  return encode_tensor_map(m, sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                           ptr, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+template <typename R, int MODE>
+int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out) {
+  constexpr int NA = (MODE == 0) ? 4 : 8;
+  const size_t smem = (size_t)NA * kRing * kPL * sizeof(R);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FV_CUDA(cudaFuncSetAttribute(k_stencil_z<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  // TMA needs 16-byte aligned rows and base addresses; small grids take the cp.async path
+  CUtensorMap tq, tv;
+  std::memset(&tq, 0, sizeof(tq));
+  std::memset(&tv, 0, sizeof(tv));
+  int use_tma = ((g->nx * sizeof(R)) % 16 == 0 && g->nx >= 64 && g->ny >= 16 && ((uintptr_t)q % 16) == 0 &&
+                 ((uintptr_t)v % 16) == 0) ? 1 : 0;
+  if (use_tma && (state_map<R>(g, q, &tq) != FV_OK || state_map<R>(g, v, &tv) != FV_OK)) use_tma = 0;
+  dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTY - 1) / kTY, (g->nz + kZChunk - 1) / kZChunk);
   ProfScope ps(g, PROF_STENCIL);
-  k_stencil<R, 0><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, (R)Gr, (R)(1.0 / g->Pr), R(0), q, q, F);
+  k_stencil_z<R, MODE><<<grid, kTX * kTY, smem, g->stream>>>(tq, tv, use_tma, g->ws.err, geo_of<R>(g), (int)g->N,
+                                                             (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
 
 template <typename R>
+int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F) {
+  return launch_stencil_z<R, 0>(g, Gr, 0.0, q, q, F);
+}
+
+template <typename R>
 int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out) {
-  dim3 grid, block;
-  cell_grid(g, grid, block);
-  ProfScope ps(g, PROF_STENCIL);
-  k_stencil<R, 1><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
+  return launch_stencil_z<R, 1>(g, Gr, sigma, q, v, out);
 }
 
 template <typename R>

@@ -50,7 +50,8 @@ class fv_arnoldi_opts(C.Structure):
 class fv_arnoldi_report(C.Structure):
     _fields_ = [("status", C.c_int), ("nconv", C.c_int), ("restarts", C.c_int), ("matvecs", C.c_longlong),
                 ("residual", C.c_double * 64), ("lam_scaled_re", C.c_double * 64),
-                ("lam_scaled_im", C.c_double * 64), ("degrees", C.c_int * 256), ("seconds", C.c_double)]
+                ("lam_scaled_im", C.c_double * 64), ("degrees", C.c_int * 256), ("seconds", C.c_double),
+                ("restarts_low", C.c_int), ("matvecs_low", C.c_longlong)]
 
 
 _lib = None
