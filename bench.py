@@ -192,8 +192,8 @@ def run_steps(fv, g, prec, q, ya, yb, K, stream, sigma, profile=False):
     for _ in range(K):
         tn = 1.0 / (2.0 * s - c2 * tau)
         # yb <- 2 tn (A - d) ya - c2 tau tn yb   (A = P(J - sigma) + sigma)
-        fv.fv_jvp_project_lincomb(g, prec, GR, sigma, q, ya, yb, 2.0 * tn, -2.0 * tn * d, -c2 * tau * tn, yb)
-        nrm = fv.fv_dot(g, prec, yb, yb)
+        nrm = fv.fv_jvp_project_lincomb(g, prec, GR, sigma, q, ya, yb, 2.0 * tn, -2.0 * tn * d, -c2 * tau * tn, yb,
+                                        want_norm=True)
         if nrm > 1e30 or nrm < 1e-30:
             sc = 1.0 / nrm ** 0.5
             fv.fv_axpby(g, prec, 0.0, yb, sc, yb)
@@ -247,31 +247,47 @@ def gpu_arm(args, ws, rank, local):
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    if dom == "transform":
-        flops = 2.0 * N * n                               # one n x n matrix along one axis of an N-cell field
+    hbm_src = "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    if dom == "transform_tc":
+        # algorithmic FLOPs of one pass: an n x n matrix applied along one axis of an N-cell field
+        flops = 2.0 * N * n
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * (1.1 / 2.25)   # TF32 dense = bf16 dense x nominal ratio 1.1 / 2.25 PFLOP/s
+        roof = {"kernel": "k_transform_tc (tcgen05 fast-diagonalisation pass, 3 x TF32 split)", "bound": "tensor",
+                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if "bf16_tflops" in peaks
+                                else "fallback 1.9 PF bf16 x 1.1/2.25"),
+                "executed_tflops": round(3 * achieved, 2)}
+        traffic_bytes = 2 * N * 4
+    elif dom == "transform":
+        flops = 2.0 * N * n
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"kernel": "k_transform<float> (fast-diagonalisation transform)", "bound": "alu",
+        roof = {"kernel": "k_transform (SIMT fast-diagonalisation pass)", "bound": "alu",
                 "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": "FP32 FMA lanes x 2 x 152 SMs x 2070 MHz (unit counts and max clock)"}
         traffic_bytes = 2 * N * 4
     else:
-        bytes_per = {"stencil": 12 * N * 4, "correct": 9 * N * 4, "divergence": 4 * N * 4}.get(dom, 2 * 4 * N * 4)
+        bytes_per = {"stencil": 12 * N * 4, "correct": 17 * N * 4, "divergence": 4 * N * 4}.get(dom, 2 * 4 * N * 4)
         achieved = bytes_per / (per_launch_ms * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "peak_source": hbm_src}
+        names = {"stencil": "k_stencil_z<float,1> (J.v)", "correct": "k_correct<float>"}
+        roof = {"kernel": names.get(dom, dom), "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "peak_source": hbm_src}
         traffic_bytes = bytes_per
     roof["traffic"] = measured_traffic(dom, n)
     roof["algorithmic_bytes"] = traffic_bytes
     roof["launch_ms"] = round(per_launch_ms, 4)
     st_ms, st_n = prof["stencil"]
     st_gbs = 12 * N * 4 / (st_ms / st_n * 1e-3) / 1e9
-    hbm_stencil = {"kernel": "k_stencil<float,1> (J.v)", "achieved": round(st_gbs, 1), "peak": hbm_peak,
+    hbm_stencil = {"kernel": "k_stencil_z<float,1> (J.v)", "achieved": round(st_gbs, 1), "peak": hbm_peak,
                    "unit": "GB/s", "frac": round(st_gbs / hbm_peak, 4), "algorithmic_bytes": 12 * N * 4,
-                   "launch_ms": round(st_ms / st_n, 4)}
-    step_bytes = (12 + 1 + 2 * 6 + 1 + 11) * N * 4   # stencil, divergence, 6 transforms r+w, correction, dot
+                   "launch_ms": round(st_ms / st_n, 4), "traffic": measured_traffic("stencil", n)}
+    # algorithmic bytes of one step: stencil 12 N, divergence 4 N, six passes 2 N each, correction 17 N
+    # (the norm is summed inside the correction pass)
+    step_bytes = (12 + 4 + 12 + 17) * N * 4
     breakdown = {k: {"ms_per_step": round(v[0] / K, 4), "launches_per_step": v[1] / K} for k, v in prof.items()}
 
     # e2e through the C-ABI with host buffers: H2D of the step's input vector, the step, D2H of the result
@@ -292,7 +308,7 @@ def e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream):
     Ke = max(3, min(K, 10))
     for _ in range(2):
         ya.copy_(host_in, non_blocking=True)
-        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb)
+        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb, want_norm=True)
         host_out.copy_(yb, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -300,8 +316,7 @@ def e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream):
     e0.record(stream)
     for _ in range(Ke):
         ya.copy_(host_in, non_blocking=True)
-        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb)
-        fv.fv_dot(g, fv.FV_FP32, yb, yb)
+        fv.fv_jvp_project_lincomb(g, fv.FV_FP32, GR, sigma, q, ya, None, 1.0, 0.0, 0.0, yb, want_norm=True)
         host_out.copy_(yb, non_blocking=True)
     e1.record(stream)
     e1.synchronize()

@@ -113,9 +113,12 @@ int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma,
 /* Fused recurrence step (the Chebyshev filter's three-term recurrence, Section 1 ref. 21):
  *     out = alpha (P (J(q) v - sigma v) + sigma v) + beta v + gamma w
  * with the axpys folded into the projection's correction pass.  w may be NULL
- * (gamma ignored) and out may alias w, not q or v.  Errors: FV_EINVAL, FV_ECUDA. */
+ * (gamma ignored) and out may alias w, not q or v.  out_norm2 (host, may be
+ * NULL) receives ||out||^2, summed in the same pass (deterministic, FP64-level
+ * accumulation) and read back with a stream synchronisation.
+ * Errors: FV_EINVAL, FV_ECUDA, FV_ENAN. */
 int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
-                           const void* w, double alpha, double beta, double gamma, void* out);
+                           const void* w, double alpha, double beta, double gamma, void* out, double* out_norm2);
 
 /* Krylov inner product <a, b> over all 4N elements, accumulated in FP64 in a
  * fixed order (bit-reproducible).  result: host.  Errors: FV_EINVAL, FV_ECUDA, FV_ENAN. */
@@ -190,6 +193,9 @@ typedef struct {
     int guard;            /* extra Ritz values kept outside the filter's ellipse */
     unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected */
     double sigma;         /* shift of the gradient complement; 0 = automatic */
+    double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-4); the phase
+                             also ends once its residual estimate has not halved in 8 restarts */
+    int low_max_restarts; /* FV_FP32: restart cap of the FP32 phase (default 100) */
 } fv_arnoldi_opts;
 
 typedef struct {
@@ -226,9 +232,10 @@ int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, const fv_arnol
  * fv_profile(g, 1) clears and starts recording, fv_profile(g, 0) stops.  fv_profile_read
  * synchronises the stream and returns, per class (host arrays of FV_PROF_CLASSES), the summed
  * milliseconds and the launch counts.  Classes: 0 stencil (F, J.v), 1 divergence, 2 pressure-solve
- * transforms, 3 gradient correction, 4 reductions, 5 other vector kernels.
+ * transforms (CUDA cores), 3 gradient correction, 4 reductions, 5 other vector kernels,
+ * 6 pressure-solve transforms on the tensor cores (FP32 data, tcgen05).
  * Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
-enum { FV_PROF_CLASSES = 6 };
+enum { FV_PROF_CLASSES = 7 };
 int fv_profile(fv_grid g, int enable);
 int fv_profile_read(fv_grid g, double* ms, long long* launches);
 

@@ -229,7 +229,7 @@ int jvp_project(fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R
 // out = alpha (P(J y - sigma y)) + beta y + gamma yprev   (one step of a three-term recurrence in A)
 template <typename R>
 int chebyshev_step(fv_grid_s* g, double Gr, double sigma, const R* q, const R* y, const R* yprev, double alpha,
-                   double beta, double gamma, R* out) {
+                   double beta, double gamma, R* out, int norm_slot) {
   FV_TRY(ensure_ws<R>(g));
   const int p = prec_index<R>();
   R* Y = (R*)g->ws.Y[p];
@@ -238,7 +238,7 @@ int chebyshev_step(fv_grid_s* g, double Gr, double sigma, const R* q, const R* y
   FV_TRY(launch_jvp<R>(g, Gr, sigma, q, y, Y));
   FV_TRY(launch_divergence<R>(g, Y, phi));
   FV_TRY(launch_poisson<R>(g, phi, phi, tmp));
-  FV_TRY(launch_correct<R>(g, Y, phi, alpha, y, beta, yprev, gamma, out));
+  FV_TRY(launch_correct<R>(g, Y, phi, alpha, y, beta, yprev, gamma, out, norm_slot));
   return FV_OK;
 }
 
@@ -658,18 +658,27 @@ int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma, const void* q, 
 }
 
 int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
-                           const void* w, double alpha, double beta, double gamma, void* out) {
+                           const void* w, double alpha, double beta, double gamma, void* out, double* out_norm2) {
   if (!g || !q || !v || !out) return invalid("null argument");
   if (out == q || out == v) return invalid("out must not alias q or v");
+  if (prec != FV_FP64 && prec != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   // alpha (P(Jv - sigma v) + sigma v) + beta v + gamma w = alpha P(Jv - sigma v) + (alpha sigma + beta) v + gamma w
   const double b2 = alpha * sigma + beta;
+  const int slot = out_norm2 ? 0 : -1;
   if (prec == FV_FP64)
-    return chebyshev_step<double>(g, Gr, sigma, (const double*)q, (const double*)v, w ? (const double*)w : nullptr,
-                                  alpha, b2, w ? gamma : 0.0, (double*)out);
-  if (prec == FV_FP32)
-    return chebyshev_step<float>(g, Gr, sigma, (const float*)q, (const float*)v, w ? (const float*)w : nullptr, alpha,
-                                 b2, w ? gamma : 0.0, (float*)out);
-  return invalid("precision must be FV_FP64 or FV_FP32");
+    FV_TRY(chebyshev_step<double>(g, Gr, sigma, (const double*)q, (const double*)v, w ? (const double*)w : nullptr,
+                                  alpha, b2, w ? gamma : 0.0, (double*)out, slot));
+  else
+    FV_TRY(chebyshev_step<float>(g, Gr, sigma, (const float*)q, (const float*)v, w ? (const float*)w : nullptr, alpha,
+                                 b2, w ? gamma : 0.0, (float*)out, slot));
+  if (out_norm2) {
+    FV_TRY(read_scalars(g, 0, 1, out_norm2));
+    if (!std::isfinite(*out_norm2)) {
+      set_error("non-finite norm");
+      return FV_ENAN;
+    }
+  }
+  return FV_OK;
 }
 
 int fv_dot(fv_grid g, int prec, const void* a, const void* b, double* result) {
@@ -715,6 +724,8 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->guard = 2;
   o->seed = 1;
   o->sigma = 0.0;
+  o->low_tol = 1e-4;
+  o->low_max_restarts = 100;
 }
 
 }  // extern "C"
@@ -891,10 +902,12 @@ static void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz
   }
 }
 
+// stall > 0: give up (FV_ENOCONV, Ritz vectors still written) once the largest relative residual estimate
+// has not halved over `stall` restarts (the FP32 phase of the mixed form stops at its round-off floor).
 template <typename R>
 static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
                         double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start = nullptr,
-                        double* lam_far_io = nullptr) {
+                        double* lam_far_io = nullptr, int stall = 0) {
   const auto t_start = std::chrono::steady_clock::now();
   const size_t n = 4 * g->N;
   const int m = o.m;
@@ -943,6 +956,8 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   std::vector<Ritz> ritz;
   std::vector<int> order;
   int status = FV_ENOCONV, nret = 0;
+  double best_est = 1e300;
+  int best_at = 0;
   for (int restart = 0; restart <= o.max_restarts; ++restart) {
     double xn2;
     FV_TRY(V.dot(x, x, &xn2));
@@ -1028,7 +1043,14 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       if (!(est[i] <= o.tol * std::max(mag, 1e-300))) all = false;
     }
     rep->restarts = restart;
-    const bool last = all || mm < m || restart == o.max_restarts;
+    double worst = 0.0;
+    for (int i = 0; i < nw; ++i) worst = std::max(worst, est[i] / std::max(std::hypot(ritz[i].re, ritz[i].im), 1e-300));
+    if (worst <= 0.5 * best_est) {
+      best_est = worst;
+      best_at = restart;
+    }
+    const bool stalled = stall > 0 && restart - best_at >= stall;
+    const bool last = all || mm < m || restart == o.max_restarts || stalled;
     if (last) {
       status = all || mm < m ? FV_OK : FV_ENOCONV;
       nret = nw;
@@ -1184,10 +1206,10 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
 
 namespace fv {
 
-// Mixed precision: FP32 Krylov vectors and J.v + projection until the Ritz residuals reach 1e-4 (with FP32
-// matvecs the residual floor is ~ u_32 ||A|| / |lam|, far above 1e-6 for the small leading eigenvalues of
-// this stiff operator), then FP64 Chebyshev-Arnoldi cycles started from the sum of the FP32 Ritz vectors
-// refine the same pairs to the requested tolerance.
+// Mixed precision: FP32 Krylov vectors and J.v + projection until the Ritz residuals reach low_tol or stop
+// improving (with FP32 matvecs the residual floor is ~ u_32 ||A|| / |lam|, far above 1e-6 for the small
+// leading eigenvalues of this stiff operator, and running on at the floor degrades the Ritz vectors), then
+// FP64 Chebyshev-Arnoldi cycles started from the sum of the FP32 Ritz vectors refine the same pairs to tol.
 static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const fv_arnoldi_opts& o, double* re,
                          double* im, void* vecs_out, fv_arnoldi_report* rep) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -1196,12 +1218,12 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   DevBuf<double> z64, t64, X64;
   FV_TRY(X32.alloc((size_t)(k + 2) * n));
   fv_arnoldi_opts o1 = o;
-  o1.tol = std::max(o.tol, 1e-4);
-  o1.max_restarts = std::min(o.max_restarts, 100);
+  o1.tol = std::max(o.tol, o.low_tol);
+  o1.max_restarts = std::max(0, std::min(o.max_restarts, o.low_max_restarts));
   fv_arnoldi_report r1;
   std::memset(&r1, 0, sizeof(r1));
   double lam_far = 0.0;
-  int st1 = arnoldi_impl<float>(g, k, Gr, q, o1, re, im, X32.p, &r1, nullptr, &lam_far);
+  int st1 = arnoldi_impl<float>(g, k, Gr, q, o1, re, im, X32.p, &r1, nullptr, &lam_far, 8);
   if (st1 != FV_OK && st1 != FV_ENOCONV) return st1;
   FV_TRY(z64.alloc(n));
   FV_TRY(t64.alloc(n));
@@ -1244,7 +1266,7 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
   else
     fv_arnoldi_default_opts(&o);
   if (k < 1 || o.m > 200 || k + o.guard + 2 > o.m || o.min_degree < 1 || o.max_degree < o.min_degree ||
-      o.max_restarts < 0 || k > 63)
+      o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)))
     return invalid("bad Arnoldi options (need 1 <= k <= 63, k + guard + 2 <= m <= 200)");
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   fv_arnoldi_report rep;

@@ -105,7 +105,15 @@ int cuda_status(cudaError_t e, const char* what);
   } while (0)
 
 // ------------------------------------------------------------------ measurement
-enum { PROF_STENCIL = 0, PROF_DIVERGENCE = 1, PROF_TRANSFORM = 2, PROF_CORRECT = 3, PROF_REDUCE = 4, PROF_VECTOR = 5 };
+enum {
+  PROF_STENCIL = 0,
+  PROF_DIVERGENCE = 1,
+  PROF_TRANSFORM = 2,
+  PROF_CORRECT = 3,
+  PROF_REDUCE = 4,
+  PROF_VECTOR = 5,
+  PROF_TRANSFORM_TC = 6
+};
 // Records a CUDA event pair around the launches in its scope when profiling is enabled.
 struct ProfScope {
   const fv_grid_s* g;
@@ -123,9 +131,10 @@ int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R*
 template <typename R>
 int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs);
 // out = alpha (Y - G phi) + beta v + gamma w   (velocity; T without G phi).  v, w may be null.
+// norm_slot >= 0: also ||out||^2 into g->ws.scalars[norm_slot] (fused block partials).
 template <typename R>
 int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, const R* v, double beta,
-                   const R* w, double gamma, R* out);
+                   const R* w, double gamma, R* out, int norm_slot = -1);
 
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>
@@ -151,6 +160,9 @@ int launch_fill_normal(const fv_grid_s* g, unsigned long long seed, R* out);
 
 constexpr int kReduceBlocks = 1024;
 constexpr int kMaxScalars = 512;
+constexpr int kPartialSlots = kReduceBlocks * 256;  // capacity of g->ws.partials
+// g->ws.scalars[slot] = sum of g->ws.partials[0 .. np) in a fixed order
+int launch_sum_partials(const fv_grid_s* g, int np, int slot);
 
 // host scalar readback: copies `count` scalars starting at `slot` and synchronises
 int read_scalars(const fv_grid_s* g, int slot, int count, double* out);
@@ -185,6 +197,6 @@ template <typename R>
 int jvp_project(fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);
 template <typename R>
 int chebyshev_step(fv_grid_s* g, double Gr, double sigma, const R* q, const R* y, const R* yprev,
-                   double alpha, double beta, double gamma, R* out);
+                   double alpha, double beta, double gamma, R* out, int norm_slot = -1);
 
 }  // namespace fv

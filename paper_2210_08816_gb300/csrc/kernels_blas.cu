@@ -175,6 +175,23 @@ __global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ part
 }
 
 // Vector updates run in the vectors' own precision (coefficients rounded to it once).
+// out[b] = sum of part[b * chunk .. min(np, (b + 1) * chunk)) in a fixed order
+__global__ void __launch_bounds__(1024) k_finish_chunks(const double* __restrict__ part, int np, int chunk,
+                                                         double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int s = blockIdx.x * chunk, e = min(np, s + chunk);
+  double v = 0.0;
+  for (int t = s + threadIdx.x; t < e; t += 1024) v += part[t];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = warp_sum(sh[lane]);
+    if (lane == 0) out[blockIdx.x] = v;
+  }
+}
+
 template <typename R>
 __global__ void k_lincomb(size_t n, int nvec, R c0, R c1, R c2, R c3, const R* x0, const R* x1, const R* x2,
                           const R* x3, R* out) {
@@ -318,6 +335,20 @@ template <typename R>
 int launch_fill_normal(const fv_grid_s* g, unsigned long long seed, R* out) {
   ProfScope ps(g, PROF_VECTOR);
   k_fill_normal<R><<<stream_grid(4 * g->N), 256, 0, g->stream>>>(g->nx, g->ny, g->nz, seed, out);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+int launch_sum_partials(const fv_grid_s* g, int np, int slot) {
+  ProfScope ps(g, PROF_REDUCE);
+  if (np > 4096) {  // two levels: 64 fixed chunks, then their sums (deterministic order)
+    const int chunk = (np + 63) / 64;
+    k_finish_chunks<<<64, 1024, 0, g->stream>>>(g->ws.partials, np, chunk, g->ws.partials + kPartialSlots - 64);
+    FV_CUDA(cudaGetLastError());
+    k_finish<false><<<1, 1024, 0, g->stream>>>(g->ws.partials + kPartialSlots - 64, 64, g->ws.scalars + slot);
+  } else {
+    k_finish<false><<<1, 1024, 0, g->stream>>>(g->ws.partials, np, g->ws.scalars + slot);
+  }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

@@ -488,30 +488,75 @@ __global__ void __launch_bounds__(256) k_divergence(Geo<R> g, int N, const R* __
 
 // out = alpha (Y - G phi) + beta v + gamma w, G phi = (phi(cell) - phi(cell - e_d)) / spacing on interior
 // faces; T gets no gradient.  Wall slots -> 0.  out may alias Y or w (each element is read, then written,
-// by the same thread).
+// by the same thread).  With part != null every block also writes the partial sum of out^2 over its cells
+// to part[linear block index] (FP32 data: compensated float pairs up to the warp, FP64 above).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = hi + x, bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_correct(Geo<R> g, int N, const R* Y, const R* __restrict__ phi,
-                                                  R alpha, const R* v, R beta, const R* w, R gamma, R* out) {
+                                                  R alpha, const R* v, R beta, const R* w, R gamma, R* out,
+                                                  double* __restrict__ part) {
   Cell<R> c;
-  if (!cell_of_thread(g, c)) return;
-  const R ph = ld(phi, c.o);
+  const bool act = cell_of_thread(g, c);
+  float shi = 0.f, slo = 0.f;  // FP32 data
+  double sd = 0.0;             // FP64 data
+  if (act) {
+    const R ph = ld(phi, c.o);
 #pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    const int o = d * N + c.o;
-    R r;
-    if (d < 3) {
-      if (c.p[d] == 0) {
-        out[o] = R(0);
-        continue;
+    for (int d = 0; d < 4; ++d) {
+      const int o = d * N + c.o;
+      R r;
+      if (d < 3) {
+        if (c.p[d] == 0) {
+          out[o] = R(0);
+          continue;
+        }
+        const R G = (ph - ld(phi, c.o - c.s[d])) * g.idc[d][c.p[d]];
+        r = alpha * (Y[o] - G);
+      } else {
+        r = alpha * Y[o];
       }
-      const R G = (ph - ld(phi, c.o - c.s[d])) * g.idc[d][c.p[d]];
-      r = alpha * (Y[o] - G);
-    } else {
-      r = alpha * Y[o];
+      if (v) r += beta * v[o];
+      if (w) r += gamma * w[o];
+      out[o] = r;
+      if (part) {
+        if (sizeof(R) == 4) {
+          const float rf = (float)r, p2 = rf * rf;
+          slo += fmaf(rf, rf, -p2);
+          two_sum_add(shi, slo, p2);
+        } else {
+          sd = fma((double)r, (double)r, sd);
+        }
+      }
     }
-    if (v) r += beta * v[o];
-    if (w) r += gamma * w[o];
-    out[o] = r;
+  }
+  if (!part) return;
+  double wsum;
+  if (sizeof(R) == 4) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, shi, off), l2 = __shfl_down_sync(0xffffffffu, slo, off);
+      slo += l2;
+      two_sum_add(shi, slo, h2);
+    }
+    wsum = (double)shi + (double)slo;
+  } else {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sd += __shfl_down_sync(0xffffffffu, sd, off);
+    wsum = sd;
+  }
+  __shared__ double wpart[8];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if ((tid & 31) == 0) wpart[tid >> 5] = wsum;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x * blockDim.y * blockDim.z) / 32; ++i) t += wpart[i];
+    part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = t;
   }
 }
 
@@ -586,12 +631,19 @@ int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs) {
 
 template <typename R>
 int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, const R* v, double beta,
-                   const R* w, double gamma, R* out) {
+                   const R* w, double gamma, R* out, int norm_slot) {
   dim3 grid, block;
   cell_grid(g, grid, block);
-  ProfScope ps(g, PROF_CORRECT);
-  k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w, (R)gamma, out);
-  FV_CUDA(cudaGetLastError());
+  const int nblocks = (int)(grid.x * grid.y * grid.z);
+  const bool want = norm_slot >= 0 && nblocks <= kPartialSlots - 64;
+  {
+    ProfScope ps(g, PROF_CORRECT);
+    k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w, (R)gamma,
+                                                out, want ? g->ws.partials : nullptr);
+    FV_CUDA(cudaGetLastError());
+  }
+  if (want) return launch_sum_partials(g, nblocks, norm_slot);
+  if (norm_slot >= 0) return launch_dot<R>(g, out, out, 4 * g->N, norm_slot);
   return FV_OK;
 }
 
@@ -601,8 +653,8 @@ template int launch_jvp<float>(const fv_grid_s*, double, double, const float*, c
 template int launch_divergence<double>(const fv_grid_s*, const double*, double*);
 template int launch_divergence<float>(const fv_grid_s*, const float*, float*);
 template int launch_correct<double>(const fv_grid_s*, const double*, const double*, double, const double*, double,
-                                    const double*, double, double*);
+                                    const double*, double, double*, int);
 template int launch_correct<float>(const fv_grid_s*, const float*, const float*, double, const float*, double,
-                                   const float*, double, float*);
+                                   const float*, double, float*, int);
 
 }  // namespace fv

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_conv[kTcStages], bar_empty[kTcStages], bar_acc;
   __shared__ uint32_t tmem_slot;
+  __shared__ float lz_s[256];  // eigenvalues of the contracted axis (scaled pass only)
   // 1024-byte aligned ring: per stage A (8 KB), A_lo (8 KB), B_hi (n x 64 B), B_lo (n x 64 B)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t b_bytes = (uint32_t)n * kTcRowBytes;
@@ -133,6 +134,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(smem_u32(&bar_acc), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (SCALE)
+    for (int m = threadIdx.x; m < n; m += kTcThreads) lz_s[m] = lz[m];
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(256)
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int j = 0; j < 16; ++j) {
             const int m = c0 + j;
             float v = __uint_as_float(r[j]);
-            if (SCALE) v = (m == 0 && pa == 0 && pb == 0) ? 0.f : v / (lz[m] + sa + sb2);
+            if (SCALE) v = (m == 0 && pa == 0 && pb == 0) ? 0.f : v * __frcp_rn(lz_s[m] + sa + sb2);
             out[(long long)m * P + p] = v;
           }
         }
@@ -386,7 +389,7 @@ int tc_pass(const fv_grid_s* g, int axis, int which, int na, int nb, const float
   const FdmDev<float>& f = g->fdm32;
   const dim3 grid((unsigned)((P + kTcBM - 1) / kTcBM));
   const size_t smem = tc_smem_bytes(n);
-  ProfScope ps(g, PROF_TRANSFORM);
+  ProfScope ps(g, PROF_TRANSFORM_TC);
   if (scale)
     k_transform_tc<true><<<grid, kTcThreads, smem, g->stream>>>(tmA, g->tc.B[axis][which], g->tc.B[axis][which + 1],
                                                                 out, (int)P, n, f.lam[0], f.lam[1], f.lam[2], nb,

@@ -44,7 +44,8 @@ class fv_newton_report(C.Structure):
 class fv_arnoldi_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("m", C.c_int), ("tol", C.c_double), ("max_restarts", C.c_int),
                 ("max_degree", C.c_int), ("min_degree", C.c_int), ("guard", C.c_int),
-                ("seed", C.c_ulonglong), ("sigma", C.c_double)]
+                ("seed", C.c_ulonglong), ("sigma", C.c_double), ("low_tol", C.c_double),
+                ("low_max_restarts", C.c_int)]
 
 
 class fv_arnoldi_report(C.Structure):
@@ -74,7 +75,7 @@ def lib():
             "fv_jvp": (i, [vp, i, d, vp, vp, vp]),
             "fv_project": (i, [vp, i, vp, i, d, C.POINTER(i), C.POINTER(d)]),
             "fv_jvp_project": (i, [vp, i, d, d, vp, vp, vp]),
-            "fv_jvp_project_lincomb": (i, [vp, i, d, d, vp, vp, vp, d, d, d, vp]),
+            "fv_jvp_project_lincomb": (i, [vp, i, d, d, vp, vp, vp, d, d, d, vp, C.POINTER(d)]),
             "fv_dot": (i, [vp, i, vp, vp, C.POINTER(d)]),
             "fv_dot_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp]),
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
@@ -102,8 +103,8 @@ EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elem
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
 
-FV_PROF_CLASSES = 6
-PROF_NAMES = ["stencil", "divergence", "transform", "correct", "reduce", "vector"]
+FV_PROF_CLASSES = 7
+PROF_NAMES = ["stencil", "divergence", "transform", "correct", "reduce", "vector", "transform_tc"]
 
 
 def _check(status: int, where: str, ok=(FV_OK,)):
@@ -202,13 +203,16 @@ def fv_jvp_project(g: Grid, prec, Gr, sigma, q, v, out):
     return out
 
 
-def fv_jvp_project_lincomb(g: Grid, prec, Gr, sigma, q, v, w, alpha, beta, gamma, out):
+def fv_jvp_project_lincomb(g: Grid, prec, Gr, sigma, q, v, w, alpha, beta, gamma, out, want_norm=False):
+    """out = alpha (P (J v - sigma v) + sigma v) + beta v + gamma w; returns ||out||^2 if want_norm."""
     dt = g.dtype(prec)
     wp = _ptr(w, dt, g.n, "w") if w is not None else None
+    nrm = C.c_double(0.0)
     _check(lib().fv_jvp_project_lincomb(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"),
                                         _ptr(v, dt, g.n, "v"), wp, float(alpha), float(beta), float(gamma),
-                                        _ptr(out, dt, g.n, "out")), "fv_jvp_project_lincomb")
-    return out
+                                        _ptr(out, dt, g.n, "out"), C.byref(nrm) if want_norm else None),
+           "fv_jvp_project_lincomb")
+    return nrm.value if want_norm else out
 
 
 def fv_dot(g: Grid, prec, a, b) -> float:

@@ -203,5 +203,9 @@ def test_fused_recurrence_step(fv, prec_name):
     A = P.full([J[c] - sigma * vf[c] for c in range(4)])
     ref = D.to_api(og, [alpha * (A[c] + sigma * vf[c]) + beta * vf[c] + gamma * wf[c] for c in range(4)])
     tw = dev(w, dt)
-    fv.fv_jvp_project_lincomb(g, prec, Gr, sigma, dev(q, dt), dev(v, dt), tw, alpha, beta, gamma, tw)
-    assert rel(host(tw, og.shape), ref) <= tol
+    nrm = fv.fv_jvp_project_lincomb(g, prec, Gr, sigma, dev(q, dt), dev(v, dt), tw, alpha, beta, gamma, tw,
+                                    want_norm=True)
+    got = host(tw, og.shape)
+    assert rel(got, ref) <= tol
+    ref_n2 = sum(float(np.sum(a * a)) for a in got)   # the fused norm is that of the stored result
+    assert nrm == pytest.approx(ref_n2, rel=1e-12)
