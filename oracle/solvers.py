@@ -285,9 +285,13 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
     tol / 100, made divergence free by `project`): a mode that a restart
     happened to lose comes back above round-off, while the noise floor it adds
     stays below the tolerance.
+    Verification: at the first convergence the restart vector gets a strong
+    random component (relative weight 1e-2); the values are accepted once the
+    iteration converges again to the same ones (at most three rounds).
     """
     rng = np.random.default_rng(seed)
     refresh = 0.01 * tol if refresh is None else refresh
+    pre, verify_left, strong = None, 3, False
     x = x0 / np.linalg.norm(x0)
     info = {"restarts": 0, "matvecs": 0, "degrees": []}
     nmv = [0]
@@ -318,12 +322,17 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
         S = S / np.linalg.norm(S, axis=0)
         est = np.abs(hm) * np.abs(S[mm - 1, :nw])
         scale = np.maximum(np.abs(theta[:nw]), 1e-300)
-        if np.all(est <= tol * scale) or mm < m or it == max_restarts:
+        conv = bool(np.all(est <= tol * scale))
+        if conv and mm == m and verify_left > 0 and it < max_restarts:
+            same = pre is not None and len(pre) == nw and np.all(np.abs(theta[:nw] - pre) <= 100 * tol * scale)
+            if not same:
+                pre, strong, verify_left, conv = theta[:nw].copy(), True, verify_left - 1, False
+        if conv or mm < m or it == max_restarts:
             X = V[:mm].T @ S[:, :nw]
             res = np.array([np.linalg.norm(A(X[:, i].real) + 1j * A(X[:, i].imag) - theta[i] * X[:, i])
                             for i in range(nw)])
             info.update(restarts=it, matvecs=nmv[0], residual=res, estimate=est,
-                        converged=bool(np.all(est <= tol * scale)))
+                        converged=bool(np.all(est <= tol * scale)) or mm < m)
             return theta[:nw], X, info
         nf = min(nw + guard, mm - 2)
         if nf < mm and abs(theta[nf - 1].imag) > 0 and np.isclose(theta[nf], np.conj(theta[nf - 1])):
@@ -345,10 +354,12 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=200, max_degree=
         for i in range(nw):
             yi = Y[:, i].real if theta[i].imag >= 0 else Y[:, i].imag
             z += yi / max(np.linalg.norm(yi), 1e-300)
-        if refresh > 0.0:
+        weight = 1e-2 if strong else refresh
+        strong = False
+        if weight > 0.0:
             r = rng.standard_normal(x.size)
             r = project(r) if project is not None else r
-            z += refresh * np.linalg.norm(z) * r / np.linalg.norm(r)
+            z += weight * np.linalg.norm(z) * r / np.linalg.norm(r)
         if trace is not None:
             trace(it, theta[:nw], est, d, c2, rate, deg)
         x = chebyshev_filter(Af, z, d, c2, lam_ref, deg)

@@ -548,8 +548,8 @@ int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out) {
   if (st == FV_OK) st = upload_axes<double>(g, ax, 0, g->geo64, g->fdm64);
   if (st == FV_OK) st = upload_axes<float>(g, ax, 1, g->geo32, g->fdm32);
   if (st == FV_OK && tc_eligible(g)) {
-    std::vector<double> Einv[3] = {ax[0].Einv, ax[1].Einv, ax[2].Einv}, E[3] = {ax[0].E, ax[1].E, ax[2].E};
-    if (tc_setup(g, Einv, E) != FV_OK) {  // keep the SIMT passes
+    std::vector<double> idx[3] = {ax[0].idx, ax[1].idx, ax[2].idx}, idc[3] = {ax[0].idc, ax[1].idc, ax[2].idc};
+    if (tc_setup(g, idx, idc) != FV_OK) {  // keep the SIMT passes
       g->tc.ready = false;
       cudaGetLastError();
     }
@@ -958,6 +958,12 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   int status = FV_ENOCONV, nret = 0;
   double best_est = 1e300;
   int best_at = 0;
+  // verification: at the first convergence the restart vector gets a strong random component (1e-2); the
+  // result is accepted once the iteration converges again to the same values (a mode that every restart
+  // had lost would show up in between)
+  bool verifying = false, strong = false;
+  int verify_left = (stall > 0) ? 0 : 3;
+  std::vector<Ritz> pre;
   for (int restart = 0; restart <= o.max_restarts; ++restart) {
     double xn2;
     FV_TRY(V.dot(x, x, &xn2));
@@ -1050,6 +1056,19 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       best_at = restart;
     }
     const bool stalled = stall > 0 && restart - best_at >= stall;
+    if (all && mm == m && verify_left > 0 && restart < o.max_restarts) {
+      bool same = verifying && (int)pre.size() == nw;
+      for (int i = 0; same && i < nw; ++i)
+        same = std::hypot(ritz[i].re - pre[i].re, ritz[i].im - pre[i].im) <=
+               100.0 * o.tol * std::max(std::hypot(ritz[i].re, ritz[i].im), 1e-300);
+      if (!same) {
+        pre.assign(ritz.begin(), ritz.begin() + nw);
+        verifying = true;
+        strong = true;
+        --verify_left;
+        all = false;
+      }
+    }
     const bool last = all || mm < m || restart == o.max_restarts || stalled;
     if (last) {
       status = all || mm < m ? FV_OK : FV_ENOCONV;
@@ -1160,8 +1179,9 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       FV_TRY(project_inplace<R>(g, w.p, 1, 0.0, nullptr, nullptr));
       FV_TRY(V.dot(z, z, &zn2));
       FV_TRY(V.dot(w.p, w.p, &rn2));
-      const double eps = 0.01 * o.tol * std::sqrt(zn2 / std::max(rn2, 1e-300));
+      const double eps = (strong ? 1e-2 : 0.01 * o.tol) * std::sqrt(zn2 / std::max(rn2, 1e-300));
       FV_TRY(V.lin(z, {{1.0, z}, {eps, w.p}}));
+      strong = false;
     }
     // three-term recurrence: y1 = tau1 (A - d) y0; y_{j+1} = 2 tau_{j+1} (A - d) y_j - c2 tau_j tau_{j+1} y_{j-1}
     const double s = lam_ref - d;

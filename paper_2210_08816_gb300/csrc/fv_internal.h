@@ -65,7 +65,9 @@ struct Profiler {
 struct TcState {
   bool ready = false;
   void* buf = nullptr;
-  CUtensorMap B[3][4];
+  // per axis: [fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi, bwd_s_lo, bwd_a_hi, bwd_a_lo]
+  CUtensorMap B[3][8];
+  const float* lam[3] = {nullptr, nullptr, nullptr};  // eigenvalues in the tensor-core mode order
 };
 }  // namespace fv
 
@@ -174,8 +176,8 @@ int encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, cons
 
 // Tensor-core pressure-solve passes (kernels_tc.cu), FP32 only.
 bool tc_eligible(const fv_grid_s* g);
-int tc_setup(fv_grid_s* g, const std::vector<double>* Einv, const std::vector<double>* E);
-int tc_pass(const fv_grid_s* g, int axis, int which, int na, int nb, const float* in, float* out, bool scale);
+int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<double>* idc);
+int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale);
 
 // ------------------------------------------------------------------ host linear algebra (host_linalg.cpp)
 // Symmetric tridiagonal eigen-decomposition (implicit QR with Wilkinson shifts).

@@ -143,13 +143,14 @@ int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp) {
 template <>
 int launch_poisson<float>(const fv_grid_s* g, const float* rhs, float* phi, float* tmp) {
   const int nx = g->nx, ny = g->ny, nz = g->nz;
-  if (g->tc.ready) {  // the same six passes on the tensor cores (3 x TF32 split, FP32 accuracy)
-    FV_TRY(tc_pass(g, 0, 0, nz, ny, rhs, tmp, false));
-    FV_TRY(tc_pass(g, 1, 0, nx, nz, tmp, phi, false));
-    FV_TRY(tc_pass(g, 2, 0, ny, nx, phi, tmp, true));
-    FV_TRY(tc_pass(g, 0, 2, nz, ny, tmp, phi, false));
-    FV_TRY(tc_pass(g, 1, 2, nx, nz, phi, tmp, false));
-    FV_TRY(tc_pass(g, 2, 2, ny, nx, tmp, phi, false));
+  if (g->tc.ready) {  // the same six passes on the tensor cores (3 x TF32 split, FP32 accuracy; modes in
+                      // the symmetric / antisymmetric order of the mirror-symmetric grid)
+    FV_TRY(tc_pass(g, 0, false, nz, ny, rhs, tmp, false));
+    FV_TRY(tc_pass(g, 1, false, nx, nz, tmp, phi, false));
+    FV_TRY(tc_pass(g, 2, false, ny, nx, phi, tmp, true));
+    FV_TRY(tc_pass(g, 0, true, nz, ny, tmp, phi, false));
+    FV_TRY(tc_pass(g, 1, true, nx, nz, phi, tmp, false));
+    FV_TRY(tc_pass(g, 2, true, ny, nx, tmp, phi, false));
     return FV_OK;
   }
   const FdmDev<float>& f = fdm_of<float>(g);

@@ -214,26 +214,61 @@ struct Ring {
 
 __host__ __device__ constexpr int unit(int d, int c) { return d == c ? 1 : 0; }
 
+// The metric values one cell uses along one axis (cell index c): x and y bundles are loaded once per
+// thread, the z bundle once per plane.
+template <typename R>
+struct AxM {
+  R ix, ixm;     // 1 / width of cells c and c-1
+  R ic, icp;     // 1 / spacing across faces c and c+1 (2 / width at a wall)
+  R wl, wr;      // interpolation weights at face c
+  R wlp, wrp;    // ... and at face c+1
+  R ic0, icn;    // faces 0 and n (walls)
+};
+
+template <typename R>
+__device__ __forceinline__ AxM<R> load_axm(const Geo<R>& g, int d, int c) {
+  AxM<R> m;
+  const int n = g.n[d];
+  m.ix = g.idx[d][c];
+  m.ixm = c >= 1 ? g.idx[d][c - 1] : R(0);
+  m.ic = g.idc[d][c];
+  m.icp = g.idc[d][c + 1];
+  m.wl = g.wl[d][c];
+  m.wr = g.wr[d][c];
+  m.wlp = c + 1 <= n ? g.wl[d][c + 1] : R(0);
+  m.wrp = c + 1 <= n ? g.wr[d][c + 1] : R(0);
+  m.ic0 = g.idc[d][0];
+  m.icn = g.idc[d][n];
+  return m;
+}
+
+template <int D, typename R>
+__device__ __forceinline__ const AxM<R>& axm(const AxM<R>& x, const AxM<R>& y, const AxM<R>& z) {
+  return D == 0 ? x : (D == 1 ? y : z);
+}
+
 // Same mathematics as momentum_terms / temperature_terms, reading neighbours from the ring.
 // Arrays 0..3 are the advecting state a, arrays AB..AB+3 the advected field b (AB = 0 for F, 4 for J.v).
 template <typename R, int C, int NA, int AB>
-__device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], R& conv, R& lap) {
+__device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], const AxM<R>& mx,
+                                              const AxM<R>& my, const AxM<R>& mz, R& conv, R& lap) {
   constexpr int cx = unit(C, 0), cy = unit(C, 1), cz = unit(C, 2);
+  const AxM<R>& MC = axm<C>(mx, my, mz);
   const int pc = p[C], nc = g.n[C];
   const R aH = S.at(C, 0, 0, 0), bH = S.at(AB + C, 0, 0, 0);
   const R aM = (pc >= 2) ? S.at(C, -cx, -cy, -cz) : R(0);
   const R bM = (pc >= 2) ? S.at(AB + C, -cx, -cy, -cz) : R(0);
   const R aP = (pc + 1 < nc) ? S.at(C, cx, cy, cz) : R(0);
   const R bP = (pc + 1 < nc) ? S.at(AB + C, cx, cy, cz) : R(0);
-  const R idcC = g.idc[C][pc];
   const R aE = R(0.5) * (aH + aP), bE = R(0.5) * (bH + bP);
   const R aW = R(0.5) * (aM + aH), bW = R(0.5) * (bM + bH);
-  conv = R(2) * (aE * bE - aW * bW) * idcC;
-  lap = ((bP - bH) * g.idx[C][pc] - (bH - bM) * g.idx[C][pc - 1]) * idcC;
-  const R wlC = g.wl[C][pc], wrC = g.wr[C][pc];
+  conv = R(2) * (aE * bE - aW * bW) * MC.ic;
+  lap = ((bP - bH) * MC.ix - (bH - bM) * MC.ixm) * MC.ic;
+  const R wlC = MC.wl, wrC = MC.wr;
 #pragma unroll
   for (int t = 1; t <= 2; ++t) {
     const int D = (C + t) % 3;
+    const AxM<R>& MD = (D == 0) ? mx : (D == 1 ? my : mz);
     const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
     const int pd = p[D], nd = g.n[D];
     R fLo = R(0), fHi = R(0), gLo, gHi;
@@ -241,60 +276,59 @@ __device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>
       const R aDc = wlC * S.at(D, -cx, -cy, -cz) + wrC * S.at(D, 0, 0, 0);
       const R bDc = wlC * S.at(AB + D, -cx, -cy, -cz) + wrC * S.at(AB + D, 0, 0, 0);
       const R bCm = S.at(AB + C, -dx, -dy, -dz), aCm = S.at(C, -dx, -dy, -dz);
-      const R aCd = g.wl[D][pd] * aCm + g.wr[D][pd] * aH;
-      const R bCd = g.wl[D][pd] * bCm + g.wr[D][pd] * bH;
+      const R aCd = MD.wl * aCm + MD.wr * aH;
+      const R bCd = MD.wl * bCm + MD.wr * bH;
       fLo = aDc * bCd + bDc * aCd;
-      gLo = (bH - bCm) * g.idc[D][pd];
+      gLo = (bH - bCm) * MD.ic;
     } else {
-      gLo = bH * g.idc[D][0];
+      gLo = bH * MD.ic0;
     }
     if (pd + 1 <= nd - 1) {
       const R aDc = wlC * S.at(D, dx - cx, dy - cy, dz - cz) + wrC * S.at(D, dx, dy, dz);
       const R bDc = wlC * S.at(AB + D, dx - cx, dy - cy, dz - cz) + wrC * S.at(AB + D, dx, dy, dz);
       const R bCp = S.at(AB + C, dx, dy, dz), aCp = S.at(C, dx, dy, dz);
-      const R aCd = g.wl[D][pd + 1] * aH + g.wr[D][pd + 1] * aCp;
-      const R bCd = g.wl[D][pd + 1] * bH + g.wr[D][pd + 1] * bCp;
+      const R aCd = MD.wlp * aH + MD.wrp * aCp;
+      const R bCd = MD.wlp * bH + MD.wrp * bCp;
       fHi = aDc * bCd + bDc * aCd;
-      gHi = (bCp - bH) * g.idc[D][pd + 1];
+      gHi = (bCp - bH) * MD.icp;
     } else {
-      gHi = -bH * g.idc[D][nd];
+      gHi = -bH * MD.icn;
     }
-    const R ixD = g.idx[D][pd];
-    conv += (fHi - fLo) * ixD;
-    lap += (gHi - gLo) * ixD;
+    conv += (fHi - fLo) * MD.ix;
+    lap += (gHi - gLo) * MD.ix;
   }
 }
 
 template <typename R, int NA, int AB>
-__device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], R T_hot,
+__device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3],
+                                                 const AxM<R>& mx, const AxM<R>& my, const AxM<R>& mz, R T_hot,
                                                  R& conv, R& lap) {
   const R TaH = S.at(3, 0, 0, 0), TbH = S.at(AB + 3, 0, 0, 0);
   conv = R(0);
   lap = R(0);
 #pragma unroll
   for (int D = 0; D < 3; ++D) {
+    const AxM<R>& MD = (D == 0) ? mx : (D == 1 ? my : mz);
     const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
     const int pd = p[D], nd = g.n[D];
     R fLo = R(0), fHi = R(0), gLo = R(0), gHi = R(0);
     if (pd >= 1) {
       const R Tam = S.at(3, -dx, -dy, -dz), Tbm = S.at(AB + 3, -dx, -dy, -dz);
-      const R wl = g.wl[D][pd], wr = g.wr[D][pd];
-      fLo = S.at(D, 0, 0, 0) * (wl * Tbm + wr * TbH) + S.at(AB + D, 0, 0, 0) * (wl * Tam + wr * TaH);
-      gLo = (TbH - Tbm) * g.idc[D][pd];
+      fLo = S.at(D, 0, 0, 0) * (MD.wl * Tbm + MD.wr * TbH) + S.at(AB + D, 0, 0, 0) * (MD.wl * Tam + MD.wr * TaH);
+      gLo = (TbH - Tbm) * MD.ic;
     } else if (D == 0) {
-      gLo = (TbH - T_hot) * g.idc[0][0];
+      gLo = (TbH - T_hot) * MD.ic0;
     }
     if (pd + 1 <= nd - 1) {
       const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
-      const R wl = g.wl[D][pd + 1], wr = g.wr[D][pd + 1];
-      fHi = S.at(D, dx, dy, dz) * (wl * TbH + wr * Tbp) + S.at(AB + D, dx, dy, dz) * (wl * TaH + wr * Tap);
-      gHi = (Tbp - TbH) * g.idc[D][pd + 1];
+      fHi = S.at(D, dx, dy, dz) * (MD.wlp * TbH + MD.wrp * Tbp) +
+            S.at(AB + D, dx, dy, dz) * (MD.wlp * TaH + MD.wrp * Tap);
+      gHi = (Tbp - TbH) * MD.icp;
     } else if (D == 0) {
-      gHi = -TbH * g.idc[0][nd];
+      gHi = -TbH * MD.icn;
     }
-    const R ixD = g.idx[D][pd];
-    conv += (fHi - fLo) * ixD;
-    lap += (gHi - gLo) * ixD;
+    conv += (fHi - fLo) * MD.ix;
+    lap += (gHi - gLo) * MD.ix;
   }
 }
 
@@ -423,10 +457,12 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
   const int i = i0 + tx, j = j0 + ty;
   const bool active = (i < nx && j < ny);
   const R half = (MODE == 0) ? R(0.5) : R(1);
+  const AxM<R> mx = load_axm(g, 0, active ? i : 0), my = load_axm(g, 1, active ? j : 0);
   for (int k = k0; k < kend; ++k) {
     if (k + 2 <= kend) issue_plane(k + 2);  // plane k+2 feeds the output plane k+1
     const bool ready = wait_plane(k + 1) && ok;
     if (active && ready) {
+      const AxM<R> mz = load_axm(g, 2, k);
       Ring<R, NA> S;
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz)
@@ -435,7 +471,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
       const int o = (k * ny + j) * nx + i;
       R conv, lap;
       if (i >= 1) {
-        momentum_ring<R, 0, NA, AB>(g, S, p, conv, lap);
+        momentum_ring<R, 0, NA, AB>(g, S, p, mx, my, mz, conv, lap);
         R r = lap - half * conv;
         if (MODE == 1) r -= sigma * S.at(AB + 0, 0, 0, 0);
         out[o] = r;
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
         out[o] = R(0);
       }
       if (j >= 1) {
-        momentum_ring<R, 1, NA, AB>(g, S, p, conv, lap);
+        momentum_ring<R, 1, NA, AB>(g, S, p, mx, my, mz, conv, lap);
         R r = lap - half * conv;
         if (MODE == 1) r -= sigma * S.at(AB + 1, 0, 0, 0);
         out[N + o] = r;
@@ -451,15 +487,15 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
         out[N + o] = R(0);
       }
       if (k >= 1) {
-        momentum_ring<R, 2, NA, AB>(g, S, p, conv, lap);
-        const R Tf = g.wl[2][k] * S.at(AB + 3, 0, 0, -1) + g.wr[2][k] * S.at(AB + 3, 0, 0, 0);
+        momentum_ring<R, 2, NA, AB>(g, S, p, mx, my, mz, conv, lap);
+        const R Tf = mz.wl * S.at(AB + 3, 0, 0, -1) + mz.wr * S.at(AB + 3, 0, 0, 0);
         R r = lap - half * conv + Gr * Tf;
         if (MODE == 1) r -= sigma * S.at(AB + 2, 0, 0, 0);
         out[2 * N + o] = r;
       } else {
         out[2 * N + o] = R(0);
       }
-      temperature_ring<R, NA, AB>(g, S, p, (MODE == 0) ? R(1) : R(0), conv, lap);
+      temperature_ring<R, NA, AB>(g, S, p, mx, my, mz, (MODE == 0) ? R(1) : R(0), conv, lap);
       R r = lap * invPr - half * conv;
       if (MODE == 1) r -= sigma * S.at(AB + 3, 0, 0, 0);
       out[3 * N + o] = r;

@@ -1,20 +1,37 @@
-// Tensor-core (tcgen05) version of one fast-diagonalisation pass for FP32 fields.
+// Tensor-core (tcgen05) version of the fast-diagonalisation passes for FP32 fields.
 //
-// The pass is the GEMM  C[p][m] = sum_k A[p][k] B[m][k]  (A = field rows, k contiguous; B = the n x n
-// 1D eigenvector matrix, k contiguous), stored transposed as out[m][p] (see kernels_fdm.cu).  FP32
-// accuracy on TF32 tensor cores by the three-product split: A = A_hi + A_lo, B = B_hi + B_lo with
+// A pass is the GEMM  C[p][m] = sum_k A[p][k] B[m][k]  (A = field rows, k contiguous; B = a 1D eigenvector
+// matrix), stored transposed as out[m][p] (see kernels_fdm.cu).
+//
+// Mirror symmetry.  The grid is symmetric about 1/2, so the 1D operators are centro-symmetric and every
+// eigenvector is either symmetric or antisymmetric.  With the modes ordered [symmetric | antisymmetric]
+// (the "tensor-core order"):
+//   forward  (cells -> modes):  phi_s = sum_{k<n/2} F_s[s][k] (r[k] + r[n-1-k]),
+//                               phi_a = sum_{k<n/2} F_a[a][k] (r[k] - r[n-1-k]);
+//   backward (modes -> cells):  S[i] = sum_s E_s[i][s] phi_s,  A[i] = sum_a E_a[i][a] phi_a  (i < n/2),
+//                               out[i] = S + A,  out[n-1-i] = S - A.
+// Each pass is then two GEMMs with K = n/2 and N = n/2: half the tensor work and half the B traffic of the
+// dense transform.  The forward sum / difference is formed in shared memory by the converter warps; the
+// backward S +- A in the epilogue.
+//
+// FP32 accuracy on TF32 tensor cores by the three-product split: A = A_hi + A_lo, B = B_hi + B_lo with
 // A_hi, B_hi exactly representable in TF32, and  A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi  (the dropped
 // A_lo B_lo and the TF32 rounding of the lo parts are ~2^-22 relative).  B_hi / B_lo are prepared on the
 // host; A is split in shared memory by the converter warps.
 //
-// One CTA = one 128-row tile of p and all n (<= 256) modes, K in slabs of 16 (one 64-byte swizzle row):
-//   warp 0      TMA producer: A slab (128 x 16) and B_hi, B_lo slabs (n x 16) into a 4-stage ring
-//   warp 1      TMEM allocation; one elected thread issues tcgen05.mma (M = 128, N = n, K = 8) x 3 x 2
-//   warps 2..5  split A into hi/lo in place, then the epilogue: tcgen05.ld rows -> out[m][p]
+// One CTA = one 128-row tile of p and all n (<= 256) outputs; per stage two 16-wide K slabs of A (slab j
+// and its mirror n/16-1-j forward, slab j and j + n/32 backward) and the matching 16-wide slabs of the two
+// half-size B matrices, in a 3-stage ring:
+//   warp 0      TMA producer
+//   warp 1      TMEM allocation; one elected thread issues tcgen05.mma (M = 128, N = n/2, K = 8): per
+//               stage 2 k-steps x 3 products x 2 halves into two accumulators (TMEM columns 0 and n/2)
+//   warps 2..5  converters (sum / difference, hi / lo split), then the epilogue: tcgen05.ld -> out[m][p]
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and drains.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -27,8 +44,8 @@ namespace {
 constexpr int kTcBM = 128;                 // rows per tile
 constexpr int kTcBK = 16;                  // fp32 elements per K slab (64 bytes: one 64-byte swizzle row)
 constexpr int kTcRowBytes = kTcBK * 4;
-constexpr int kTcABytes = kTcBM * kTcRowBytes;  // one A (or A_lo) slab
-constexpr int kTcStages = 4;
+constexpr int kTcABytes = kTcBM * kTcRowBytes;  // one A slab tile (8 KB)
+constexpr int kTcStages = 3;
 constexpr int kTcThreads = 192;
 constexpr long long kWaitLimit = 1LL << 22;  // bounded spin on every mbarrier (seconds at most)
 
@@ -107,22 +124,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <bool SCALE>
+// Converter helpers.  A 64-byte swizzled row r keeps its 16-byte chunk c at physical chunk c ^ ((r >> 1) & 3).
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ void split4(const float4 x, float4& h, float4& l) {
+  h.x = tf32_hi(x.x);
+  h.y = tf32_hi(x.y);
+  h.z = tf32_hi(x.z);
+  h.w = tf32_hi(x.w);
+  l.x = x.x - h.x;
+  l.y = x.y - h.y;
+  l.z = x.z - h.z;
+  l.w = x.w - h.w;
+}
+
+template <bool SCALE, bool BWD>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_transform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-                   const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ out, int P, int n,
+    k_transform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB1hi,
+                   const __grid_constant__ CUtensorMap tmB1lo, const __grid_constant__ CUtensorMap tmB2hi,
+                   const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int n,
                    const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
                    int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_conv[kTcStages], bar_empty[kTcStages], bar_acc;
   __shared__ uint32_t tmem_slot;
   __shared__ float lz_s[256];  // eigenvalues of the contracted axis (scaled pass only)
-  // 1024-byte aligned ring: per stage A (8 KB), A_lo (8 KB), B_hi (n x 64 B), B_lo (n x 64 B)
+  const int h = n / 2;         // outputs per half, K per half
+  // 1024-byte aligned ring; per stage tiles T0..T7: A1, A2 (loaded), A1_lo, A2_lo (converted),
+  // B1_hi, B1_lo, B2_hi, B2_lo (loaded, h rows x 64 B each)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t b_bytes = (uint32_t)n * kTcRowBytes;
-  const uint32_t stage_bytes = 2u * kTcABytes + 2u * b_bytes;
+  const uint32_t b_bytes = (uint32_t)h * kTcRowBytes;
+  const uint32_t stage_bytes = 4u * kTcABytes + 4u * b_bytes;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = n / kTcBK;
+  const int nst = n / (2 * kTcBK);  // stages per tile: pairs of slabs
   const int p0 = blockIdx.x * kTcBM;
 
   if (threadIdx.x == 0) {
@@ -149,73 +186,101 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
-      for (int s = 0; s < nk; ++s) {
-        const int st = s % kTcStages;
-        if (s >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((s / kTcStages) - 1) & 1, err, 1)) break;
+      for (int j = 0; j < nst; ++j) {
+        const int st = j % kTcStages;
+        if (j >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((j / kTcStages) - 1) & 1, err, 1)) break;
         const uint32_t sb = base + st * stage_bytes;
         const uint32_t fb = smem_u32(&bar_full[st]);
-        mbar_expect_tx(fb, kTcABytes + 2u * b_bytes);
-        tma_load_2d(sb, &tmA, fb, s * kTcBK, p0);
-        tma_load_2d(sb + 2u * kTcABytes, &tmBhi, fb, s * kTcBK, 0);
-        tma_load_2d(sb + 2u * kTcABytes + b_bytes, &tmBlo, fb, s * kTcBK, 0);
+        const int k1 = j * kTcBK;
+        const int k2 = BWD ? h + j * kTcBK : n - kTcBK - j * kTcBK;
+        mbar_expect_tx(fb, 2u * kTcABytes + 4u * b_bytes);
+        tma_load_2d(sb, &tmA, fb, k1, p0);
+        tma_load_2d(sb + kTcABytes, &tmA, fb, k2, p0);
+        tma_load_2d(sb + 4u * kTcABytes, &tmB1hi, fb, j * kTcBK, 0);
+        tma_load_2d(sb + 4u * kTcABytes + b_bytes, &tmB1lo, fb, j * kTcBK, 0);
+        tma_load_2d(sb + 4u * kTcABytes + 2u * b_bytes, &tmB2hi, fb, j * kTcBK, 0);
+        tma_load_2d(sb + 4u * kTcABytes + 3u * b_bytes, &tmB2lo, fb, j * kTcBK, 0);
         ++issued;
       }
       // drain: every issued copy has landed before the block may exit
-      for (int s = (issued > kTcStages ? issued - kTcStages : 0); s < issued; ++s)
-        mbar_wait(smem_u32(&bar_full[s % kTcStages]), (s / kTcStages) & 1, err, 2);
+      for (int j = (issued > kTcStages ? issued - kTcStages : 0); j < issued; ++j)
+        mbar_wait(smem_u32(&bar_full[j % kTcStages]), (j / kTcStages) & 1, err, 2);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
+      const uint32_t idesc =
+          (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(h >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
       bool ok = true;
-      for (int s = 0; s < nk && ok; ++s) {
-        const int st = s % kTcStages;
-        ok = mbar_wait(smem_u32(&bar_conv[st]), (s / kTcStages) & 1, err, 3);
+      for (int j = 0; j < nst && ok; ++j) {
+        const int st = j % kTcStages;
+        ok = mbar_wait(smem_u32(&bar_conv[st]), (j / kTcStages) & 1, err, 3);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sb = base + st * stage_bytes;
 #pragma unroll
-        for (int kk = 0; kk < kTcBK / 8; ++kk) {
-          const uint64_t ahi = smem_desc(sb + kk * 32), alo = smem_desc(sb + kTcABytes + kk * 32);
-          const uint64_t bhi = smem_desc(sb + 2u * kTcABytes + kk * 32);
-          const uint64_t blo = smem_desc(sb + 2u * kTcABytes + b_bytes + kk * 32);
-          mma_tf32(tmem, ahi, bhi, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem, ahi, blo, idesc, 1u);
-          mma_tf32(tmem, alo, bhi, idesc, 1u);
+        for (int half = 0; half < 2; ++half) {
+          const uint32_t a_hi = sb + half * kTcABytes, a_lo = sb + (2 + half) * kTcABytes;
+          const uint32_t b_hi = sb + 4u * kTcABytes + (2 * half) * b_bytes, b_lo = b_hi + b_bytes;
+          const uint32_t d = tmem + (uint32_t)(half * h);
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 8; ++kk) {
+            const uint64_t ahi = smem_desc(a_hi + kk * 32), alo = smem_desc(a_lo + kk * 32);
+            const uint64_t bhi = smem_desc(b_hi + kk * 32), blo = smem_desc(b_lo + kk * 32);
+            mma_tf32(d, ahi, bhi, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, ahi, blo, idesc, 1u);
+            mma_tf32(d, alo, bhi, idesc, 1u);
+          }
         }
         mma_commit(smem_u32(&bar_empty[st]));
       }
       mma_commit(smem_u32(&bar_acc));  // arrives once every MMA issued above has completed
     }
   } else {
-    // converters: thread t splits row t of the A slab (64 bytes, whatever its swizzled position)
+    // converters: thread t owns row t of the stage's A tiles
     const int t = threadIdx.x - 64;
+    const int x = (t >> 1) & 3;  // swizzle pattern of this row
     bool ok = true;
-    for (int s = 0; s < nk; ++s) {
-      const int st = s % kTcStages;
-      ok = mbar_wait(smem_u32(&bar_full[st]), (s / kTcStages) & 1, err, 4);
+    for (int j = 0; j < nst; ++j) {
+      const int st = j % kTcStages;
+      ok = mbar_wait(smem_u32(&bar_full[st]), (j / kTcStages) & 1, err, 4);
       if (!ok) break;
-      const uint32_t sb = base + st * stage_bytes;
-      float4* a = reinterpret_cast<float4*>(smem_raw + (sb - smem_u32(smem_raw)) + t * kTcRowBytes);
-      float4* alo = reinterpret_cast<float4*>(smem_raw + (sb - smem_u32(smem_raw)) + kTcABytes + t * kTcRowBytes);
+      unsigned char* sp = smem_raw + ((base + st * stage_bytes) - smem_u32(smem_raw)) + t * kTcRowBytes;
+      float4* a1 = reinterpret_cast<float4*>(sp);
+      float4* a2 = reinterpret_cast<float4*>(sp + kTcABytes);
+      float4* l1 = reinterpret_cast<float4*>(sp + 2 * kTcABytes);
+      float4* l2 = reinterpret_cast<float4*>(sp + 3 * kTcABytes);
+      if (BWD) {  // plain hi / lo split of both slabs
 #pragma unroll
-      for (int c = 0; c < kTcRowBytes / 16; ++c) {
-        float4 x = a[c], h, l;
-        uint32_t u;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x.x));
-        h.x = __uint_as_float(u);
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x.y));
-        h.y = __uint_as_float(u);
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x.z));
-        h.z = __uint_as_float(u);
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x.w));
-        h.w = __uint_as_float(u);
-        l.x = x.x - h.x;
-        l.y = x.y - h.y;
-        l.z = x.z - h.z;
-        l.w = x.w - h.w;
-        a[c] = h;
-        alo[c] = l;
+        for (int c = 0; c < 4; ++c) {
+          float4 hh, ll;
+          split4(a1[c], hh, ll);
+          a1[c] = hh;
+          l1[c] = ll;
+          split4(a2[c], hh, ll);
+          a2[c] = hh;
+          l2[c] = ll;
+        }
+      } else {  // r[k] +- r[n-1-k]: logical chunk c of slab j pairs with logical chunk 3-c of the mirror slab,
+                // element e with element 3-e
+        float4 av[4], mv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          av[c] = a1[c ^ x];
+          mv[c] = a2[(3 - c) ^ x];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 a = av[c], m = mv[c];
+          const float4 sum = make_float4(a.x + m.w, a.y + m.z, a.z + m.y, a.w + m.x);
+          const float4 dif = make_float4(a.x - m.w, a.y - m.z, a.z - m.y, a.w - m.x);
+          float4 hh, ll;
+          split4(sum, hh, ll);
+          a1[c ^ x] = hh;
+          l1[c ^ x] = ll;
+          split4(dif, hh, ll);
+          a2[c ^ x] = hh;
+          l2[c ^ x] = ll;
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&bar_conv[st]));
@@ -236,16 +301,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         sa = ly[pa];
         sb2 = lx[pb];
       }
-      for (int c0 = 0; c0 < n; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      for (int c0 = 0; c0 < h; c0 += 16) {
+        uint32_t r1[16], r2[16];
+        tmem_ld16(lane_base + (uint32_t)c0, r1);
+        tmem_ld16(lane_base + (uint32_t)(h + c0), r2);
         if (p < P) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int m = c0 + j;
-            float v = __uint_as_float(r[j]);
-            if (SCALE) v = (m == 0 && pa == 0 && pb == 0) ? 0.f : v * __frcp_rn(lz_s[m] + sa + sb2);
-            out[(long long)m * P + p] = v;
+          for (int jj = 0; jj < 16; ++jj) {
+            const int m = c0 + jj;
+            const float v1 = __uint_as_float(r1[jj]), v2 = __uint_as_float(r2[jj]);
+            if (BWD) {  // cells m and n-1-m
+              out[(long long)m * P + p] = v1 + v2;
+              out[(long long)(n - 1 - m) * P + p] = v1 - v2;
+            } else if (SCALE) {  // symmetric mode m, antisymmetric mode h + m
+              const float s1 = (m == 0 && pa == 0 && pb == 0) ? 0.f : v1 * __frcp_rn(lz_s[m] + sa + sb2);
+              out[(long long)m * P + p] = s1;
+              out[(long long)(h + m) * P + p] = v2 * __frcp_rn(lz_s[h + m] + sa + sb2);
+            } else {
+              out[(long long)m * P + p] = v1;
+              out[(long long)(h + m) * P + p] = v2;
+            }
           }
         }
       }
@@ -315,7 +391,7 @@ int encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, cons
 
 namespace {
 
-size_t tc_smem_bytes(int n) { return (size_t)kTcStages * (2 * kTcABytes + 2 * (size_t)n * kTcRowBytes) + 1024; }
+size_t tc_smem_bytes(int n) { return (size_t)kTcStages * (4 * kTcABytes + 4 * (size_t)(n / 2) * kTcRowBytes) + 1024; }
 
 }  // namespace
 
@@ -326,39 +402,95 @@ bool tc_eligible(const fv_grid_s* g) {
   return encoder() != nullptr;
 }
 
-// B operands: per axis the forward (E^-1) and backward (E) matrices split into TF32-exact hi and the
-// FP32 remainder lo, in one device buffer: [axis][fwd_hi, fwd_lo, bwd_hi, bwd_lo][n x n].
-int tc_setup(fv_grid_s* g, const std::vector<double>* Einv, const std::vector<double>* E) {
-  size_t total = 0;
+// B operands in the tensor-core order of the modes ([symmetric | antisymmetric], each by decreasing
+// eigenvalue), built from the two half-size problems of the mirror-symmetric 1D operator: in the symmetric
+// form B = W^-1/2 S W^-1/2 (tridiagonal d, e) the restriction to vectors with y[i] = +-y[n-1-i] is the
+// leading (n/2) x (n/2) block with its last diagonal entry d[h-1] +- e[h-1] (the coupling across the
+// midpoint).  Their eigenvectors, continued by mirror symmetry and scaled by 1/sqrt(2), are orthonormal
+// eigenvectors of B that are exactly symmetric / antisymmetric (a full eigensolver returns arbitrary
+// mixtures of the nearly degenerate wall-localised pairs of a stretched grid).  Per axis and direction
+// two (h x h) matrices, each as TF32-exact hi and FP32 remainder:
+//   forward  F_s[s][k] = sqrt(w_k / 2) y_s[k],   F_a[a][k] = sqrt(w_k / 2) y_a[k]     (k < h)
+//   backward E_s[i][s] = y_s[i] / sqrt(2 w_i),   E_a[i][a] = y_a[i] / sqrt(2 w_i)     (i < h)
+// plus the eigenvalues in that order.  Buffer: [axis][fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi,
+// bwd_s_lo, bwd_a_hi, bwd_a_lo][h x h], then [axis][lambda (n)].
+int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<double>* idc) {
   const int ns[3] = {g->nx, g->ny, g->nz};
-  for (int d = 0; d < 3; ++d) total += 4 * (size_t)ns[d] * ns[d];
-  std::vector<float> h(total);
+  size_t total = 0;
+  for (int d = 0; d < 3; ++d) total += 8 * (size_t)(ns[d] / 2) * (ns[d] / 2) + ns[d];
+  std::vector<float> hbuf(total);
   size_t o = 0;
-  size_t off[3][4];
-  auto split = [&](const std::vector<double>& M, size_t n2) {
-    const size_t ohi = o, olo = o + n2;
-    for (size_t i = 0; i < n2; ++i) {
+  size_t moff[3][8], loff[3];
+  auto put_split = [&](const std::vector<double>& M, size_t& ohi, size_t& olo, size_t cnt) {
+    ohi = o;
+    olo = o + cnt;
+    for (size_t i = 0; i < cnt; ++i) {
       const float f = (float)M[i];
       uint32_t u;
       std::memcpy(&u, &f, 4);
-      // round to nearest TF32 (10 explicit mantissa bits): add half of the dropped range, clear it
-      u = (u + 0x1000u) & 0xFFFFE000u;
+      u = (u + 0x1000u) & 0xFFFFE000u;  // round to nearest TF32 (10 explicit mantissa bits)
       float hi;
       std::memcpy(&hi, &u, 4);
-      h[ohi + i] = hi;
-      h[olo + i] = (float)(M[i] - (double)hi);
+      hbuf[ohi + i] = hi;
+      hbuf[olo + i] = (float)(M[i] - (double)hi);
     }
-    o += 2 * n2;
-    return std::make_pair(ohi, olo);
+    o += 2 * cnt;
   };
+  std::vector<double> lam_tc[3];
   for (int d = 0; d < 3; ++d) {
-    const size_t n2 = (size_t)ns[d] * ns[d];
-    auto f = split(Einv[d], n2);
-    auto b = split(E[d], n2);
-    off[d][0] = f.first;
-    off[d][1] = f.second;
-    off[d][2] = b.first;
-    off[d][3] = b.second;
+    const int n = ns[d], h = n / 2;
+    std::vector<double> w(n), dg(n), off(n, 0.0);
+    for (int i = 0; i < n; ++i) w[i] = 1.0 / idx[d][i];
+    for (int i = 0; i < n; ++i) {
+      double sdiag = 0.0;
+      if (i >= 1) sdiag -= idc[d][i];
+      if (i + 1 <= n - 1) sdiag -= idc[d][i + 1];
+      dg[i] = sdiag / w[i];
+      if (i + 1 <= n - 1) off[i] = idc[d][i + 1] / std::sqrt(w[i] * w[i + 1]);
+    }
+    std::vector<double> Ys, Ya, ls, la;
+    for (int part = 0; part < 2; ++part) {
+      std::vector<double> dd(dg.begin(), dg.begin() + h), ee(std::max(h - 1, 1), 0.0), Q;
+      for (int i = 0; i + 1 < h; ++i) ee[i] = off[i];
+      dd[h - 1] += (part == 0 ? 1.0 : -1.0) * off[h - 1];
+      if (!tridiag_eig(h, dd, ee, Q)) return FV_EINVAL;
+      std::vector<int> ord(h);
+      for (int i = 0; i < h; ++i) ord[i] = i;
+      std::sort(ord.begin(), ord.end(), [&](int a, int b) { return dd[a] > dd[b]; });
+      std::vector<double> Y((size_t)h * h), L(h);
+      for (int c = 0; c < h; ++c) {
+        L[c] = dd[ord[c]];
+        for (int i = 0; i < h; ++i) Y[(size_t)i * h + c] = Q[(size_t)i * h + ord[c]];
+      }
+      if (part == 0) {
+        L[0] = 0.0;  // the constant vector: an exact null vector of the Neumann operator
+        Ys = Y;
+        ls = L;
+      } else {
+        Ya = Y;
+        la = L;
+      }
+    }
+    const size_t hh = (size_t)h * h;
+    std::vector<double> Fs(hh), Fa(hh), Es(hh), Ea(hh);
+    const double r2 = 1.0 / std::sqrt(2.0);
+    for (int r = 0; r < h; ++r)
+      for (int c = 0; c < h; ++c) {
+        Fs[(size_t)r * h + c] = r2 * std::sqrt(w[c]) * Ys[(size_t)c * h + r];  // [mode r][cell c]
+        Fa[(size_t)r * h + c] = r2 * std::sqrt(w[c]) * Ya[(size_t)c * h + r];
+        Es[(size_t)r * h + c] = r2 * Ys[(size_t)r * h + c] / std::sqrt(w[r]);  // [cell r][mode c]
+        Ea[(size_t)r * h + c] = r2 * Ya[(size_t)r * h + c] / std::sqrt(w[r]);
+      }
+    put_split(Fs, moff[d][0], moff[d][1], hh);
+    put_split(Fa, moff[d][2], moff[d][3], hh);
+    put_split(Es, moff[d][4], moff[d][5], hh);
+    put_split(Ea, moff[d][6], moff[d][7], hh);
+    lam_tc[d] = ls;
+    lam_tc[d].insert(lam_tc[d].end(), la.begin(), la.end());
+  }
+  for (int d = 0; d < 3; ++d) {
+    loff[d] = o;
+    for (int m = 0; m < ns[d]; ++m) hbuf[o++] = (float)lam_tc[d][m];
   }
   void* buf = nullptr;
   if (cudaMalloc(&buf, total * sizeof(float)) != cudaSuccess) {
@@ -367,37 +499,40 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* Einv, const std::vector<do
     return FV_ENOMEM;
   }
   g->tc.buf = buf;
-  FV_CUDA(cudaMemcpy(buf, h.data(), total * sizeof(float), cudaMemcpyHostToDevice));
-  for (int d = 0; d < 3; ++d)
-    for (int j = 0; j < 4; ++j) {
-      const float* p = (const float*)buf + off[d][j];
-      FV_TRY(encode(&g->tc.B[d][j], p, ns[d], ns[d], ns[d]));
-    }
+  FV_CUDA(cudaMemcpy(buf, hbuf.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  for (int d = 0; d < 3; ++d) {
+    const int h = ns[d] / 2;
+    for (int j = 0; j < 8; ++j) FV_TRY(encode(&g->tc.B[d][j], (const float*)buf + moff[d][j], h, h, h));
+    g->tc.lam[d] = (const float*)buf + loff[d];
+  }
   const int smem_max = (int)tc_smem_bytes(256);
-  FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  FV_CUDA(cudaFuncSetAttribute(k_transform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   g->tc.ready = true;
   return FV_OK;
 }
 
-// one pass: in[a][b][k] (na*nb rows of n) -> out[m][a][b], with the matrix of `axis` (which = 0 forward, 2 backward)
-int tc_pass(const fv_grid_s* g, int axis, int which, int na, int nb, const float* in, float* out, bool scale) {
+// one pass: in[a][b][k] (na*nb rows of n) -> out[m][a][b] with the matrices of `axis`; bwd selects the
+// backward (modes -> cells) matrices.  Mode indices are in the tensor-core order throughout.
+int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale) {
   const int n = (axis == 0) ? g->nx : (axis == 1) ? g->ny : g->nz;
   const long long P = (long long)na * nb;
   CUtensorMap tmA;
   FV_TRY(encode(&tmA, in, P, n, kTcBM));
-  const FdmDev<float>& f = g->fdm32;
   const dim3 grid((unsigned)((P + kTcBM - 1) / kTcBM));
   const size_t smem = tc_smem_bytes(n);
+  const CUtensorMap* B = g->tc.B[axis] + (bwd ? 4 : 0);
   ProfScope ps(g, PROF_TRANSFORM_TC);
-  if (scale)
-    k_transform_tc<true><<<grid, kTcThreads, smem, g->stream>>>(tmA, g->tc.B[axis][which], g->tc.B[axis][which + 1],
-                                                                out, (int)P, n, f.lam[0], f.lam[1], f.lam[2], nb,
-                                                                g->ws.err);
+  if (bwd)
+    k_transform_tc<false, true><<<grid, kTcThreads, smem, g->stream>>>(tmA, B[0], B[1], B[2], B[3], out, (int)P, n,
+                                                                       nullptr, nullptr, nullptr, nb, g->ws.err);
+  else if (scale)
+    k_transform_tc<true, false><<<grid, kTcThreads, smem, g->stream>>>(
+        tmA, B[0], B[1], B[2], B[3], out, (int)P, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb, g->ws.err);
   else
-    k_transform_tc<false><<<grid, kTcThreads, smem, g->stream>>>(tmA, g->tc.B[axis][which], g->tc.B[axis][which + 1],
-                                                                 out, (int)P, n, f.lam[0], f.lam[1], f.lam[2], nb,
-                                                                 g->ws.err);
+    k_transform_tc<false, false><<<grid, kTcThreads, smem, g->stream>>>(tmA, B[0], B[1], B[2], B[3], out, (int)P, n,
+                                                                        nullptr, nullptr, nullptr, nb, g->ws.err);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
