@@ -29,7 +29,7 @@ def main():
             break
         G *= 2.0
     x0 = np.random.default_rng(3).standard_normal(D.n_unknowns(g))
-    lam, _, info = SV.leading_eigenvalues(g, Gr, q, k=4, m=20, seed_vector=x0, tol=1e-9, max_restarts=400)
+    lam, _, info = SV.leading_eigenvalues(g, Gr, q, k=4, m=20, seed_vector=x0, tol=1e-9)
     assert info["converged"], info
     out = os.path.join(HERE, "config0_eigs_32.txt")
     with open(out, "w") as f:

@@ -8,6 +8,11 @@
   -(1/Pr) sum_d 4 n_d^2 sin^2(k_d pi / 2 n_d) (Dirichlet in x, Neumann in y, z).
 * At Gr > 0 the Arnoldi eigenvalues match a dense eigen-solve of P J restricted
   to an orthonormal basis of the divergence-free subspace.
+* On a normal matrix with a known, stiff spectrum (||A|| / |lam| ~ 500) the
+  Arnoldi on the Chebyshev-filtered operator returns the five leading
+  eigenvalues to round-off in at most three cycles, including one whose
+  eigenvector the start vector lacks, while m Arnoldi steps on A itself
+  leave every Ritz residual far above the tolerance.
 * Newton converges quadratically to a state with P F = 0, D u = 0, and the
   three symmetry measures of Eqs. 7-9 at round-off (the paper quotes "order
   1e-9" for symmetric solutions, Section 2).
@@ -110,6 +115,35 @@ def test_newton_then_arnoldi_match_dense_eigensolve():
     assert info["converged"]
     k = len(lam)
     assert np.allclose(lam, lam_dense[:k], rtol=1e-8, atol=0), (lam, lam_dense[:k + 2])
+
+
+def test_arnoldi_on_the_filtered_operator_reaches_round_off_on_a_stiff_matrix():
+    # A = Q B Q^T, Q orthogonal: eigenvalues -1, -2, -2.5, -3 +- 4i and 115 values in [-500, -5], so that
+    # ||A|| / |lam_wanted| ~ 500 as for the cube's operator; the start vector lacks the eigenvector of -2.5
+    rng = np.random.default_rng(7)
+    n = 120
+    B = np.zeros((n, n))
+    B[0, 0], B[1, 1], B[4, 4] = -2.5, -2.0, -1.0
+    B[2:4, 2:4] = [[-3.0, 4.0], [-4.0, -3.0]]
+    B[np.arange(5, n), np.arange(5, n)] = -np.linspace(5.0, 500.0, n - 5)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ B @ Q.T
+    x0 = rng.standard_normal(n)
+    x0 -= Q[:, 0] * (Q[:, 0] @ x0)
+    expect = np.array([-1.0, -2.0, -2.5, -3.0 + 4.0j, -3.0 - 4.0j])
+    lam, X, info = SV.chebyshev_arnoldi(lambda v: A @ v, x0, k=4, m=20, tol=1e-12)
+    assert info["converged"] and info["restarts"] <= 3
+    assert np.allclose(lam, expect, rtol=1e-11, atol=0), lam
+    for i in range(len(lam)):
+        assert np.linalg.norm(A @ X[:, i] - lam[i] * X[:, i]) <= 1e-12 * abs(lam[i]) * np.linalg.norm(X[:, i])
+    # the same start through m Arnoldi steps on A itself: the round-off in the stiff directions grows by
+    # ~||A|| / |lam| per step and the best Ritz residual stays many orders above the tolerance
+    V, H, mm = SV.arnoldi(lambda v: A @ v, x0 / np.linalg.norm(x0), 20)
+    th, S = np.linalg.eig(H[:mm, :mm])
+    Xa = V[:mm].T @ (S / np.linalg.norm(S, axis=0))
+    best = min(np.linalg.norm(A @ Xa[:, i] - th[i] * Xa[:, i]) / abs(th[i])
+               for i in range(mm) if np.min(np.abs(expect - th[i])) < 0.5)
+    assert best > 1e-9
 
 
 def test_conduction_nusselt_and_energy():
