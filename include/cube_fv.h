@@ -181,21 +181,21 @@ int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_newton_opts* o
 /* ---------------------------------------------------------------- Arnoldi */
 typedef struct {
     int precision;        /* FV_FP64, or FV_FP32: a phase with FP32 Krylov vectors and
-                             J.v + projection (FP64 Hessenberg, Gram-Schmidt coefficients and
-                             inner products) down to residual 1e-4, then FP64 cycles started
-                             from its Ritz vectors refine to tol */
+                             J.v + projection (FP64 Rayleigh-Ritz matrix, Gram-Schmidt
+                             coefficients and inner products) down to residual low_tol, then
+                             FP64 cycles started from its Ritz vectors refine to tol */
     int m;                /* Krylov subspace dimension per cycle */
     double tol;           /* stop when every wanted Ritz pair has
-                             ||A x - lam x|| <= tol |lam| (Arnoldi estimate) */
-    int max_restarts;
-    int max_degree;       /* Chebyshev filter degree cap per restart */
-    int min_degree;
-    int guard;            /* extra Ritz values kept outside the filter's ellipse */
+                             ||A x - lam x|| <= tol |lam| ||x|| (true residual, FP64 reductions) */
+    int max_restarts;     /* cycle cap (default 30) */
+    int max_degree;       /* Chebyshev polynomial degree cap per cycle (default 200) */
+    int min_degree;       /* (default 10) */
+    int guard;            /* extra Ritz values kept outside the filter's ellipse (default 2) */
     unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected */
     double sigma;         /* shift of the gradient complement; 0 = automatic */
     double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-4); the phase
-                             also ends once its residual estimate has not halved in 8 restarts */
-    int low_max_restarts; /* FV_FP32: restart cap of the FP32 phase (default 100) */
+                             also ends once its largest residual has not halved in 3 cycles */
+    int low_max_restarts; /* FV_FP32: cycle cap of the FP32 phase (default 20) */
 } fv_arnoldi_opts;
 
 typedef struct {
@@ -205,9 +205,9 @@ typedef struct {
     long long matvecs;
     double residual[64];  /* ||A x - lam x|| / |lam| per returned value (FP64 recomputation) */
     double lam_scaled_re[64], lam_scaled_im[64];   /* lam / sqrt(Gr): the paper's scaling */
-    int degrees[256];     /* Chebyshev degree per restart */
+    int degrees[256];     /* Chebyshev degree per cycle */
     double seconds;
-    int restarts_low;     /* FV_FP32: restarts of the FP32 phase (included in restarts) */
+    int restarts_low;     /* FV_FP32: cycles of the FP32 phase (included in restarts) */
     long long matvecs_low;/* FV_FP32: J.v + projections of the FP32 phase (included in matvecs) */
 } fv_arnoldi_report;
 
@@ -216,7 +216,11 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o);
 /* Leading eigenvalues (largest real part) of the linearised problem about
  * the steady state q: lam v = J(q) v - G p, D v = 0, i.e. of P J(q) on the
  * divergence-free subspace, by Chebyshev-preconditioned Arnoldi (Section 1
- * methods paragraph and its ref. 21; Section 4.1 uses four).  q: device
+ * methods paragraph and its ref. 21; Section 4.1 uses four): cycle 0 runs m
+ * Arnoldi steps on A = P(J - sigma) + sigma, every later cycle m steps on
+ * p(A), the Chebyshev polynomial of an ellipse around the unwanted Ritz
+ * values, with the eigenvalues of A from the Rayleigh-Ritz matrix V^T A V.
+ * q: device
  * double[4N].  re, im: host double[k+1] (a conjugate pair straddling the cut
  * is completed, so up to k+1 values; report->nconv says how many), ordered by
  * real part descending, then +Im first.  vecs: NULL or a device buffer of

@@ -277,7 +277,7 @@ def _real_parts(X, theta, idx):
 
 
 def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=50, max_degree=200, min_degree=10,
-                      guard=2, power_steps=30, project=None, refresh=1e-3, seed=12345, trace=None,
+                      guard=2, power_steps=30, project=None, refresh=None, seed=12345, trace=None,
                       amplification=1e2):
     """Leading k eigenpairs (largest real part) of A by Chebyshev-preconditioned Arnoldi.
 
@@ -286,7 +286,8 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=50, max_degree=2
     residual norms ||A x - lam x|| and the restart history.
 
     Cycle 0 runs m Arnoldi steps on A itself; every later cycle runs m Arnoldi
-    steps on the preconditioned operator B = p(A), the Chebyshev polynomial
+    steps, from p(A) applied to its start vector, on the preconditioned
+    operator B = p(A), the Chebyshev polynomial
     p(z) = T_n((z - d)/c) / T_n((lam_ref - d)/c) of the current ellipse, which
     is small on the unwanted part of the spectrum and large on the wanted part.
     The eigenvalues of A come from the Rayleigh-Ritz projection G = V^T A V on
@@ -297,8 +298,9 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=50, max_degree=2
     ones outside it; its degree gives the slowest guard value an advantage
     `amplification` over the ellipse.  The next cycle starts from the sum of
     the normalised wanted Ritz vectors plus a random component of relative
-    weight `refresh` (made divergence free by `project`), so that a mode the
-    start lacked is present in the Krylov space of B.
+    weight `refresh` (default tol / 100, made divergence free by `project`), so
+    that a mode the start lacked is present in the Krylov space of B, while the
+    noise it brings stays below the tolerance.
 
     Running the Arnoldi on B rather than on A matters for this stiff operator:
     with ||A|| / |lam_wanted| ~ 1e2 .. 1e4 every Arnoldi step on A multiplies
@@ -308,6 +310,7 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=50, max_degree=2
     interior of the ellipse instead.
     """
     rng = np.random.default_rng(seed)
+    refresh = 0.01 * tol if refresh is None else refresh
     x = x0 / np.linalg.norm(x0)
     info = {"restarts": 0, "matvecs": 0, "degrees": []}
     nmv = [0]
@@ -332,7 +335,10 @@ def chebyshev_arnoldi(A, x0, k=4, m=20, tol=1e-10, max_restarts=50, max_degree=2
             V, H, mm = arnoldi(Af, x, m)
             G = H[:mm, :mm]                      # V^T A V for a Krylov basis of A
         else:
-            V, _, mm = arnoldi(lambda v: chebyshev_filter(Af, v, *filt), x, m)
+            # start from p(A) x: the restart vector's error in the stiff directions would otherwise sit in
+            # v_1 alone, where no later Krylov vector of B (which damps those directions) can cancel it
+            x = chebyshev_filter(Af, x, *filt)
+            V, _, mm = arnoldi(lambda v: chebyshev_filter(Af, v, *filt), x / np.linalg.norm(x), m)
             AV = np.array([Af(V[j]) for j in range(mm)])
             G = V[:mm] @ AV.T                    # G[i, j] = v_i . A v_j
         theta, S = np.linalg.eig(G)

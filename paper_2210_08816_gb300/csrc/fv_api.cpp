@@ -718,14 +718,14 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->precision = FV_FP64;
   o->m = 20;
   o->tol = 1e-9;
-  o->max_restarts = 200;
+  o->max_restarts = 30;
   o->max_degree = 200;
   o->min_degree = 10;
   o->guard = 2;
   o->seed = 1;
   o->sigma = 0.0;
   o->low_tol = 1e-4;
-  o->low_max_restarts = 100;
+  o->low_max_restarts = 20;
 }
 
 }  // extern "C"
@@ -902,18 +902,41 @@ static void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz
   }
 }
 
-// stall > 0: give up (FV_ENOCONV, Ritz vectors still written) once the largest relative residual estimate
-// has not halved over `stall` restarts (the FP32 phase of the mixed form stops at its round-off floor).
+// Chebyshev polynomial p(z) = T_deg((z - d)/c) / T_deg((lam_ref - d)/c) of one cycle's ellipse.
+struct ChebFilter {
+  bool on = false;
+  double d = 0.0, c2 = 0.0, lam_ref = 0.0;
+  int deg = 0;
+};
+
+// State one Arnoldi run hands to the next (the FP32 phase of the mixed form to its FP64 phase).
+struct ArnoldiCarry {
+  double lam_far = 0.0;
+  ChebFilter filt;
+};
+
+// Advantage per application of p(A) that the degree gives the slowest guard value over the ellipse.
+constexpr double kFilterGain = 1e2;
+
+// Chebyshev-preconditioned Arnoldi.  Cycle 0 runs m Arnoldi steps on A itself; every later cycle runs m
+// steps on B = p(A) (each application = deg J.v + projection steps of the three-term recurrence), which
+// maps the stiff part of the spectrum into the small interior of the ellipse instead of amplifying its
+// round-off by ||A|| / |lam| per step.  Eigenvalues of A come from the Rayleigh-Ritz matrix G = V^T A V
+// (m more products), the k with the largest real part are tested by their true FP64 residuals, and the
+// next cycle starts from p(A) applied to the sum of the normalised wanted Ritz vectors plus a random
+// component (relative weight tol / 100) under the next ellipse.
+// stall > 0: give up (FV_ENOCONV, Ritz vectors still written) once the largest relative residual has not
+// halved over `stall` cycles (the FP32 phase of the mixed form stops at its round-off floor).
 template <typename R>
 static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
                         double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start = nullptr,
-                        double* lam_far_io = nullptr, int stall = 0) {
+                        ArnoldiCarry* carry = nullptr, int stall = 0) {
   const auto t_start = std::chrono::steady_clock::now();
   const size_t n = 4 * g->N;
   const int m = o.m;
   const bool mixed = !std::is_same<R, double>::value;
   const double sigma = (o.sigma != 0.0) ? o.sigma : g->sigma_default;
-  DevBuf<R> qR, Vb, w, y0, y1;
+  DevBuf<R> qR, Vb, w, y0, y1, X;
   if (mixed) {
     FV_TRY(qR.alloc(n));
     FV_TRY(launch_convert(g, n, q64, (float*)qR.p));
@@ -923,10 +946,11 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   FV_TRY(w.alloc(n));
   FV_TRY(y0.alloc(n));
   FV_TRY(y1.alloc(n));
+  FV_TRY(X.alloc((size_t)(std::min(k, m) + 2) * n));  // wanted Ritz vectors: real and imaginary parts
   Vec<R> V{g, n};
   long long mv = 0;
   Operator<R> A{g, Gr, sigma, q, &mv};
-  // start vector: seeded N(0,1), projected, normalised
+  // start vector: seeded N(0,1) (or the caller's), projected
   R* x = y0.p;
   if (start) {
     FV_TRY(V.copy(x, start));
@@ -934,9 +958,9 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     FV_TRY(launch_fill_normal<R>(g, o.seed, x));
   }
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
-  // far end of the spectrum: Rayleigh quotient of a short power iteration (filtered restarts stop
+  // far end of the spectrum: Rayleigh quotient of a short power iteration (the Krylov spaces of B stop
   // showing it, and the Chebyshev polynomial grows fast outside its ellipse)
-  double lam_far = (lam_far_io && *lam_far_io != 0.0) ? *lam_far_io : 0.0;
+  double lam_far = (carry && carry->lam_far != 0.0) ? carry->lam_far : 0.0;
   if (lam_far == 0.0) {
     R* z = y1.p;
     double zn2;
@@ -949,29 +973,68 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       FV_TRY(V.dot(w.p, w.p, &wn2));
       FV_TRY(V.lin(z, {{1.0 / std::sqrt(wn2), w.p}}));
     }
-    if (lam_far_io) *lam_far_io = lam_far;
   }
-  std::vector<double> H((size_t)(m + 1) * m), h(m + 1), hre, him, ycoef;
+  ChebFilter filt = carry ? carry->filt : ChebFilter{};
+
+  // out = p(A) in by the three-term recurrence
+  //   y_1 = tau_1 (A - d) y_0,  y_{j+1} = 2 tau_{j+1} (A - d) y_j - c^2 tau_j tau_{j+1} y_{j-1},
+  //   tau_1 = 1 / (lam_ref - d),  tau_{j+1} = 1 / (2 (lam_ref - d) - c^2 tau_j);
+  // y0, y1 are scratch, the input is only read.
+  auto apply_filter = [&](const R* in, R* out) -> int {
+    const double s = filt.lam_ref - filt.d;
+    double tau = 1.0 / s;
+    FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, in, nullptr, tau, tau * (sigma - filt.d), 0.0, y0.p));
+    ++mv;
+    const R* yp = in;
+    R* yc = y0.p;
+    for (int j = 1; j < filt.deg; ++j) {
+      const double tn = 1.0 / (2.0 * s - filt.c2 * tau);
+      R* dst = (yp == in) ? y1.p : const_cast<R*>(yp);  // y_{j+1} overwrites y_{j-1} (never the input)
+      FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yc, yp, 2.0 * tn, 2.0 * tn * (sigma - filt.d), -filt.c2 * tau * tn,
+                               dst));
+      ++mv;
+      yp = yc;
+      yc = dst;
+      tau = tn;
+      if (j % 16 == 0) {  // keep both terms of the recurrence in range (yp is scratch by now)
+        double nn;
+        FV_TRY(V.dot(yc, yc, &nn));
+        nn = std::sqrt(nn);
+        if (nn > 1e30 || nn < 1e-30) {
+          FV_TRY(V.lin(yc, {{1.0 / nn, yc}}));
+          FV_TRY(V.lin(const_cast<R*>(yp), {{1.0 / nn, yp}}));
+        }
+      }
+    }
+    return V.copy(out, yc);
+  };
+
+  std::vector<double> H((size_t)(m + 1) * m), h(m + 1), G, Hg, Qg, hre, him, ycoef, sh;
   std::vector<std::vector<double>> Y;
   std::vector<Ritz> ritz;
-  std::vector<int> order;
   int status = FV_ENOCONV, nret = 0;
-  double best_est = 1e300;
+  double best = 1e300;
   int best_at = 0;
-  // verification: at the first convergence the restart vector gets a strong random component (1e-2); the
-  // result is accepted once the iteration converges again to the same values (a mode that every restart
-  // had lost would show up in between)
-  bool verifying = false, strong = false;
-  int verify_left = (stall > 0) ? 0 : 3;
-  std::vector<Ritz> pre;
   for (int restart = 0; restart <= o.max_restarts; ++restart) {
+    // ---- m Arnoldi steps (CGS2) on A (first cycle) or on B = p(A) from p(A) x: the restart vector's error
+    // in the stiff directions would otherwise sit in v_1 alone, where no later Krylov vector of B (which
+    // damps those directions) can cancel it, and every Ritz vector would inherit it
+    if (filt.on) {
+      FV_TRY(V.copy(Vb.p, x));
+      FV_TRY(apply_filter(Vb.p, w.p));
+      x = w.p;
+    }
     double xn2;
     FV_TRY(V.dot(x, x, &xn2));
     FV_TRY(V.lin(Vb.p, {{1.0 / std::sqrt(xn2), x}}));
     std::fill(H.begin(), H.end(), 0.0);
     int mm = m;
     for (int j = 0; j < m; ++j) {
-      FV_TRY(A.apply(Vb.p + (size_t)j * n, w.p));
+      const R* vj = Vb.p + (size_t)j * n;
+      if (filt.on)
+        FV_TRY(apply_filter(vj, w.p));
+      else
+        FV_TRY(A.apply(vj, w.p));
       for (int pass = 0; pass < 2; ++pass) {
         FV_TRY(launch_multidot<R>(g, Vb.p, n, j + 1, w.p, n, 1));
         FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, j + 1, g->ws.scalars + 1, w.p, n));
@@ -994,11 +1057,32 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
       }
       FV_TRY(V.lin(Vb.p + (size_t)(j + 1) * n, {{1.0 / wn, w.p}}));
     }
-    if (!hessenberg_eigvals(mm, H.data(), m, hre, him)) {
+    // ---- Rayleigh-Ritz matrix G = V^T A V (for a Krylov basis of A it is the Hessenberg matrix itself)
+    G.assign((size_t)mm * mm, 0.0);
+    if (!filt.on) {
+      for (int i = 0; i < mm; ++i)
+        for (int j = 0; j < mm; ++j) G[(size_t)i * mm + j] = H[(size_t)i * m + j];
+    } else {
+      for (int j = 0; j < mm; ++j) {
+        FV_TRY(A.apply(Vb.p + (size_t)j * n, w.p));
+        FV_TRY(launch_multidot<R>(g, Vb.p, n, mm, w.p, n, 1));
+        FV_TRY(read_scalars(g, 1, mm, h.data()));
+        for (int i = 0; i < mm; ++i) {
+          if (!std::isfinite(h[i])) {
+            set_error("non-finite Rayleigh-Ritz entry");
+            return FV_ENAN;
+          }
+          G[(size_t)i * mm + j] = h[i];
+        }
+      }
+    }
+    Hg = G;
+    hessenberg_reduce(mm, Hg, Qg);
+    if (!hessenberg_eigvals(mm, Hg.data(), mm, hre, him)) {
       set_error("Hessenberg QR did not converge");
       return FV_ENOCONV;
     }
-    // H is real: pair each +Im value with its nearest -Im partner and make the pair exact mirrors
+    // G is real: pair each +Im value with its nearest -Im partner and make the pair exact mirrors
     // (the complex QR returns them with slightly different real parts), then sort (+Im first)
     ritz.clear();
     {
@@ -1010,19 +1094,19 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
           ritz.push_back({hre[i], 0.0});
           continue;
         }
-        int best = -1;
+        int bj = -1;
         double bd = 1e300;
         for (int j2 = 0; j2 < mm; ++j2)
           if (!used[j2] && him[j2] * him[i] < 0.0) {
             const double dd = std::hypot(hre[j2] - hre[i], him[j2] + him[i]);
             if (dd < bd) {
               bd = dd;
-              best = j2;
+              bj = j2;
             }
           }
-        if (best >= 0) {
-          used[best] = true;
-          const double r = 0.5 * (hre[i] + hre[best]), a = 0.5 * (std::fabs(him[i]) + std::fabs(him[best]));
+        if (bj >= 0) {
+          used[bj] = true;
+          const double r = 0.5 * (hre[i] + hre[bj]), a = 0.5 * (std::fabs(him[i]) + std::fabs(him[bj]));
           ritz.push_back({r, a});
           ritz.push_back({r, -a});
         } else {
@@ -1033,111 +1117,96 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     std::sort(ritz.begin(), ritz.end(), ritz_before);
     int nw = std::min(k, mm);
     if (nw < mm && ritz[nw - 1].im > 0) ++nw;
-    // Ritz vectors (in the Krylov basis) and the Arnoldi residual estimates |h_{m+1,m}| |y_m|
+    // ---- wanted Ritz vectors: eigenvectors s of G (= Qg times those of its Hessenberg form), X = V s;
+    // slot i holds Re x (real value or +Im member), slot i + 1 Im x for a conjugate pair
     Y.assign(nw, {});
-    const double hlast = (mm < m + 1) ? H[(size_t)mm * m + (mm - 1)] : 0.0;
-    bool all = true;
-    std::vector<double> est(nw);
     for (int i = 0; i < nw; ++i) {
-      if (!hessenberg_eigvec(mm, H.data(), m, ritz[i].re, std::fabs(ritz[i].im), Y[i])) {
+      if (!hessenberg_eigvec(mm, Hg.data(), mm, ritz[i].re, std::fabs(ritz[i].im), sh)) {
         set_error("Ritz vector inverse iteration failed");
         return FV_ENOCONV;
       }
-      const double ymr = Y[i][2 * (mm - 1)], ymi = Y[i][2 * (mm - 1) + 1];
-      est[i] = std::fabs(hlast) * std::hypot(ymr, ymi);
-      const double mag = std::hypot(ritz[i].re, ritz[i].im);
-      if (!(est[i] <= o.tol * std::max(mag, 1e-300))) all = false;
+      Y[i].assign(2 * (size_t)mm, 0.0);
+      for (int r = 0; r < mm; ++r)
+        for (int c = 0; c < mm; ++c) {
+          Y[i][2 * r] += Qg[(size_t)r * mm + c] * sh[2 * c];
+          Y[i][2 * r + 1] += Qg[(size_t)r * mm + c] * sh[2 * c + 1];
+        }
+    }
+    ycoef.assign(mm, 0.0);
+    for (int i = 0; i < nw; ++i) {
+      const bool cplx = ritz[i].im != 0.0;
+      for (int part = 0; part < (cplx ? 2 : 1); ++part) {
+        const int slot = i + part;
+        if (slot >= nw) break;
+        for (int t = 0; t < mm; ++t) ycoef[t] = -Y[i][2 * t + part];
+        FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, ycoef.data(), sizeof(double) * mm, cudaMemcpyHostToDevice,
+                                g->stream));
+        R* xs = X.p + (size_t)slot * n;
+        FV_TRY(V.zero(xs));
+        FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, xs, n));
+        FV_CUDA(cudaStreamSynchronize(g->stream));
+      }
+      if (cplx) ++i;
+    }
+    // ---- true residuals ||A x - lam x|| / (|lam| ||x||), FP64 reductions
+    bool all = true;
+    double worst = 0.0;
+    std::vector<double> xnorm(nw, 1.0);
+    for (int i = 0; i < nw; ++i) {
+      const bool cplx = ritz[i].im != 0.0;
+      const double lr = ritz[i].re, li = ritz[i].im;
+      R* xr = X.p + (size_t)i * n;
+      R* xi = (cplx && i + 1 < nw) ? X.p + (size_t)(i + 1) * n : nullptr;
+      double nr2 = 0.0, ni2 = 0.0, res2 = 0.0, t;
+      FV_TRY(V.dot(xr, xr, &nr2));
+      FV_TRY(A.apply(xr, w.p));  // A xr - (lr xr - li xi)
+      if (xi) {
+        FV_TRY(V.dot(xi, xi, &ni2));
+        FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}, {li, xi}}));
+      } else {
+        FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}}));
+      }
+      FV_TRY(V.dot(w.p, w.p, &t));
+      res2 += t;
+      if (xi) {
+        FV_TRY(A.apply(xi, w.p));  // A xi - (lr xi + li xr)
+        FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xi}, {-li, xr}}));
+        FV_TRY(V.dot(w.p, w.p, &t));
+        res2 += t;
+      }
+      const double xn = std::sqrt(nr2 + ni2), lam = std::hypot(lr, li);
+      const double rel = std::sqrt(res2) / (std::max(lam, 1e-300) * std::max(xn, 1e-300));
+      re[i] = lr;
+      im[i] = li;
+      if (i < 64) rep->residual[i] = rel;
+      xnorm[i] = xn;
+      if (xi) {
+        re[i + 1] = lr;
+        im[i + 1] = -li;
+        if (i + 1 < 64) rep->residual[i + 1] = rel;
+        xnorm[i + 1] = xn;
+      }
+      if (!(rel <= o.tol)) all = false;
+      worst = std::max(worst, rel);
+      if (cplx) ++i;
     }
     rep->restarts = restart;
-    double worst = 0.0;
-    for (int i = 0; i < nw; ++i) worst = std::max(worst, est[i] / std::max(std::hypot(ritz[i].re, ritz[i].im), 1e-300));
-    if (worst <= 0.5 * best_est) {
-      best_est = worst;
+    if (worst <= 0.5 * best) {
+      best = worst;
       best_at = restart;
     }
     const bool stalled = stall > 0 && restart - best_at >= stall;
-    if (all && mm == m && verify_left > 0 && restart < o.max_restarts) {
-      bool same = verifying && (int)pre.size() == nw;
-      for (int i = 0; same && i < nw; ++i)
-        same = std::hypot(ritz[i].re - pre[i].re, ritz[i].im - pre[i].im) <=
-               100.0 * o.tol * std::max(std::hypot(ritz[i].re, ritz[i].im), 1e-300);
-      if (!same) {
-        pre.assign(ritz.begin(), ritz.begin() + nw);
-        verifying = true;
-        strong = true;
-        --verify_left;
-        all = false;
-      }
-    }
-    const bool last = all || mm < m || restart == o.max_restarts || stalled;
-    if (last) {
+    if (all || mm < m || restart == o.max_restarts || stalled) {
       status = all || mm < m ? FV_OK : FV_ENOCONV;
       nret = nw;
-      // Ritz vectors V y (Re, Im) into the output slots, then the FP64 residual ||A x - lam x|| / |lam|
-      DevBuf<R> X;
-      FV_TRY(X.alloc((size_t)(nw + 1) * n));
-      ycoef.assign(mm, 0.0);
-      for (int i = 0; i < nw; ++i) {
-        const bool cplx = ritz[i].im != 0.0;
-        const int src = i;
-        for (int part = 0; part < (cplx ? 2 : 1); ++part) {
-          const int slot = i + part;
-          if (slot >= nw) break;
-          for (int t = 0; t < mm; ++t) ycoef[t] = -Y[src][2 * t + part];
-          FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, ycoef.data(), sizeof(double) * mm, cudaMemcpyHostToDevice,
-                                  g->stream));
-          R* xs = X.p + (size_t)slot * n;
-          FV_TRY(V.zero(xs));
-          FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, xs, n));
-          FV_CUDA(cudaStreamSynchronize(g->stream));
-        }
-        if (cplx) ++i;
-      }
-      for (int i = 0; i < nw; ++i) {
-        const bool cplx = ritz[i].im != 0.0;
-        const double lr = ritz[i].re, li = ritz[i].im;
-        R* xr = X.p + (size_t)i * n;
-        R* xi = cplx ? X.p + (size_t)(i + 1) * n : nullptr;
-        double nr2 = 0.0, ni2 = 0.0, res2 = 0.0;
-        FV_TRY(V.dot(xr, xr, &nr2));
-        FV_TRY(A.apply(xr, w.p));  // A xr - (lr xr - li xi)
-        if (cplx) {
-          FV_TRY(V.dot(xi, xi, &ni2));
-          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}, {li, xi}}));
-        } else {
-          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}}));
-        }
-        double t;
-        FV_TRY(V.dot(w.p, w.p, &t));
-        res2 += t;
-        if (cplx) {
-          FV_TRY(A.apply(xi, w.p));  // A xi - (lr xi + li xr)
-          FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xi}, {-li, xr}}));
-          FV_TRY(V.dot(w.p, w.p, &t));
-          res2 += t;
-        }
-        const double xn = std::sqrt(nr2 + ni2), lam = std::hypot(lr, li);
-        const double rel = std::sqrt(res2) / (std::max(lam, 1e-300) * std::max(xn, 1e-300));
-        re[i] = lr;
-        im[i] = li;
-        if (i < 64) rep->residual[i] = rel;
-        if (cplx && i + 1 < nw) {
-          re[i + 1] = lr;
-          im[i + 1] = -li;
-          if (i + 1 < 64) rep->residual[i + 1] = rel;
-        }
-        // normalise the stored vector(s) to unit norm of the complex vector
-        const double sc = 1.0 / std::max(xn, 1e-300);
-        FV_TRY(V.lin(xr, {{sc, xr}}));
-        if (cplx) FV_TRY(V.lin(xi, {{sc, xi}}));
-        if (cplx) ++i;
-      }
+      // unit norm of each (complex) vector
+      for (int i = 0; i < nw; ++i) FV_TRY(V.lin(X.p + (size_t)i * n, {{1.0 / std::max(xnorm[i], 1e-300), X.p + (size_t)i * n}}));
       if (vecs_out)
         FV_CUDA(cudaMemcpyAsync(vecs_out, X.p, sizeof(R) * n * nw, cudaMemcpyDeviceToDevice, g->stream));
       FV_CUDA(cudaStreamSynchronize(g->stream));
       break;
     }
-    // Chebyshev filter: wanted + guard Ritz values outside the ellipse, the rest inside
+    // ---- next ellipse: wanted + guard Ritz values outside, the rest and the far end inside
     int nf = std::min(nw + o.guard, mm - 2);
     if (nf < mm && nf >= 1 && ritz[nf - 1].im > 0) ++nf;
     nf = std::max(nf, nw);
@@ -1147,68 +1216,35 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     unwanted.push_back({1.05 * left, 0.0});
     double d = 0, c2 = 0, rate = 0;
     best_ellipse(wanted, unwanted, d, c2, rate);
-    int deg = o.min_degree;
-    if (rate > 1.0) deg = (int)std::ceil(std::log(1e8) / std::log(rate));
+    int deg = o.max_degree;
+    if (rate > 1.0) deg = (int)std::ceil(std::log(kFilterGain) / std::log(rate));
     deg = std::max(o.min_degree, std::min(o.max_degree, deg));
     if (restart < 256) rep->degrees[restart] = deg;
     double lam_ref = -1e300;
     for (auto& wv : wanted) lam_ref = std::max(lam_ref, wv.re);
-    // z = sum of the normalised wanted Ritz vectors (real part, or imaginary part of the -Im partner)
-    ycoef.assign(mm, 0.0);
-    for (int i = 0; i < nw; ++i) {
-      const bool cplx = ritz[i].im != 0.0;
-      for (int part = 0; part < (cplx ? 2 : 1); ++part) {
-        double nrm = 0.0;
-        for (int t = 0; t < mm; ++t) nrm += Y[i][2 * t + part] * Y[i][2 * t + part];
-        nrm = std::sqrt(nrm);
-        if (nrm > 0)
-          for (int t = 0; t < mm; ++t) ycoef[t] -= Y[i][2 * t + part] / nrm;
-      }
-      if (cplx) ++i;
-    }
-    FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, ycoef.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, g->stream));
+    filt = ChebFilter{true, d, c2, lam_ref, deg};
+    // ---- next start: sum of the normalised wanted Ritz vectors + a divergence-free random component (a mode
+    // the start lacked is then present in the Krylov space of B; the noise stays below the tolerance)
     R* z = y0.p;
     FV_TRY(V.zero(z));
-    FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, z, n));
-    FV_CUDA(cudaStreamSynchronize(g->stream));
-    // a small divergence-free random component (relative weight tol / 100): a mode that a restart happened
-    // to lose comes back above round-off, while the noise floor stays below the tolerance
+    for (int i = 0; i < nw; ++i) {
+      double t2;
+      FV_TRY(V.dot(X.p + (size_t)i * n, X.p + (size_t)i * n, &t2));
+      if (t2 > 0.0) FV_TRY(V.lin(z, {{1.0, z}, {1.0 / std::sqrt(t2), X.p + (size_t)i * n}}));
+    }
     {
       double zn2, rn2;
       FV_TRY(launch_fill_normal<R>(g, o.seed + 1000003ULL * (unsigned long long)(restart + 1), w.p));
       FV_TRY(project_inplace<R>(g, w.p, 1, 0.0, nullptr, nullptr));
       FV_TRY(V.dot(z, z, &zn2));
       FV_TRY(V.dot(w.p, w.p, &rn2));
-      const double eps = (strong ? 1e-2 : 0.01 * o.tol) * std::sqrt(zn2 / std::max(rn2, 1e-300));
-      FV_TRY(V.lin(z, {{1.0, z}, {eps, w.p}}));
-      strong = false;
+      FV_TRY(V.lin(z, {{1.0, z}, {0.01 * o.tol * std::sqrt(zn2 / std::max(rn2, 1e-300)), w.p}}));
     }
-    // three-term recurrence: y1 = tau1 (A - d) y0; y_{j+1} = 2 tau_{j+1} (A - d) y_j - c2 tau_j tau_{j+1} y_{j-1}
-    const double s = lam_ref - d;
-    double tau = 1.0 / s;
-    R* yp = y0.p;  // y_{j-1}
-    R* yc = y1.p;  // y_j
-    FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yp, nullptr, tau, tau * (sigma - d), 0.0, yc));
-    ++mv;
-    for (int j = 1; j < deg; ++j) {
-      const double tn = 1.0 / (2.0 * s - c2 * tau);
-      // y_{j+1} overwrites y_{j-1}
-      FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yc, yp, 2.0 * tn, 2.0 * tn * (sigma - d), -c2 * tau * tn, yp));
-      ++mv;
-      std::swap(yp, yc);
-      tau = tn;
-      if (j % 16 == 0) {
-        double nn;
-        FV_TRY(V.dot(yc, yc, &nn));
-        nn = std::sqrt(nn);
-        if (nn > 1e30 || nn < 1e-30) {
-          FV_TRY(V.lin(yc, {{1.0 / nn, yc}}));
-          FV_TRY(V.lin(yp, {{1.0 / nn, yp}}));
-        }
-      }
-    }
-    if (yc != y0.p) FV_TRY(V.copy(y0.p, yc));
-    x = y0.p;
+    x = z;
+  }
+  if (carry) {
+    carry->lam_far = lam_far;
+    carry->filt = filt;
   }
   rep->matvecs = mv;
   rep->nconv = nret;
@@ -1228,8 +1264,8 @@ namespace fv {
 
 // Mixed precision: FP32 Krylov vectors and J.v + projection until the Ritz residuals reach low_tol or stop
 // improving (with FP32 matvecs the residual floor is ~ u_32 ||A|| / |lam|, far above 1e-6 for the small
-// leading eigenvalues of this stiff operator, and running on at the floor degrades the Ritz vectors), then
-// FP64 Chebyshev-Arnoldi cycles started from the sum of the FP32 Ritz vectors refine the same pairs to tol.
+// leading eigenvalues of this stiff operator), then FP64 cycles started from the sum of the FP32 Ritz
+// vectors, under the last FP32 ellipse, refine the same pairs to tol.
 static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const fv_arnoldi_opts& o, double* re,
                          double* im, void* vecs_out, fv_arnoldi_report* rep) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -1242,8 +1278,8 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   o1.max_restarts = std::max(0, std::min(o.max_restarts, o.low_max_restarts));
   fv_arnoldi_report r1;
   std::memset(&r1, 0, sizeof(r1));
-  double lam_far = 0.0;
-  int st1 = arnoldi_impl<float>(g, k, Gr, q, o1, re, im, X32.p, &r1, nullptr, &lam_far, 8);
+  ArnoldiCarry carry;
+  int st1 = arnoldi_impl<float>(g, k, Gr, q, o1, re, im, X32.p, &r1, nullptr, &carry, 3);
   if (st1 != FV_OK && st1 != FV_ENOCONV) return st1;
   FV_TRY(z64.alloc(n));
   FV_TRY(t64.alloc(n));
@@ -1260,7 +1296,7 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   if (vecs_out) FV_TRY(X64.alloc((size_t)(k + 1) * n));
   fv_arnoldi_opts o2 = o;
   o2.precision = FV_FP64;
-  const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &lam_far);
+  const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry);
   if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
     for (int i = 0; i < r2.nconv; ++i)
       FV_TRY(launch_convert(g, n, X64.p + (size_t)i * n, (float*)vecs_out + (size_t)i * n));

@@ -189,6 +189,8 @@ bool tridiag_eig(int n, std::vector<double>& d, std::vector<double>& e, std::vec
 bool hessenberg_eigvals(int m, const double* H, int ld, std::vector<double>& re, std::vector<double>& im);
 // Eigenvector of H for eigenvalue (re, im) by inverse iteration (complex).  y: 2*m (re, im interleaved).
 bool hessenberg_eigvec(int m, const double* H, int ld, double re, double im, std::vector<double>& y);
+// Householder reduction of a general m x m matrix (row-major) to upper Hessenberg H, A = Q H Q^T.
+void hessenberg_reduce(int m, std::vector<double>& A, std::vector<double>& Q);
 // Solve a small dense system A x = b (n x n row-major) with partial pivoting; false if singular.
 bool dense_solve(int n, std::vector<double> A, std::vector<double>& b);
 // Least squares min || H y - beta e1 || for the (j+1) x j Hessenberg of GMRES (row-major, ld).

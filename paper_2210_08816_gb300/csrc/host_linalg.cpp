@@ -125,13 +125,14 @@ bool hessenberg_eigvals(int m, const double* H, int ld, std::vector<double>& re,
   return true;
 }
 
-// Eigenvector of H for the eigenvalue lam by two steps of inverse iteration with (H - lam I) factored
-// by Gaussian elimination with partial pivoting (complex); lam is nudged by eps ||H|| off exact singularity.
+// Eigenvector of H for the eigenvalue lam by three steps of inverse iteration with (H - lam I) factored
+// by Gaussian elimination with partial pivoting (complex); lam is nudged by a few eps ||H|| off exact
+// singularity (the nudge is the residual ||H y - lam y|| the vector is left with, so it stays at round-off).
 bool hessenberg_eigvec(int m, const double* H, int ld, double lre, double lim, std::vector<double>& y) {
   double hn = 0.0;
   for (int i = 0; i < m; ++i)
     for (int j = std::max(0, i - 1); j < m; ++j) hn = std::max(hn, std::fabs(H[(size_t)i * ld + j]));
-  const cd lam(lre + 1e-13 * std::max(hn, 1.0), lim);
+  const cd lam(lre + 4.0 * std::numeric_limits<double>::epsilon() * std::max(hn, 1.0), lim);
   std::vector<cd> A((size_t)m * m);
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = (j >= i - 1) ? cd(H[(size_t)i * ld + j]) : cd(0.0);
@@ -181,6 +182,52 @@ bool hessenberg_eigvec(int m, const double* H, int ld, double lre, double lim, s
     y[2 * i + 1] = (lim == 0.0) ? 0.0 : v.imag();
   }
   return true;
+}
+
+// Householder reduction of a general real matrix (m x m, row-major) to upper Hessenberg form:
+// on return A holds H (zeros below the subdiagonal) and Q (m x m, row-major, orthogonal) with
+// A_in = Q H Q^T, so that an eigenvector s of H gives the eigenvector Q s of A_in.
+void hessenberg_reduce(int m, std::vector<double>& A, std::vector<double>& Q) {
+  Q.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+  std::vector<double> v(m);
+  for (int k = 0; k + 2 < m; ++k) {
+    double alpha = 0.0;
+    for (int i = k + 1; i < m; ++i) alpha += A[(size_t)i * m + k] * A[(size_t)i * m + k];
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    const double x0 = A[(size_t)(k + 1) * m + k];
+    if (x0 > 0) alpha = -alpha;  // v = x - alpha e1 with alpha of the opposite sign: no cancellation
+    double vn = 0.0;
+    for (int i = 0; i < m; ++i) v[i] = 0.0;
+    for (int i = k + 1; i < m; ++i) v[i] = A[(size_t)i * m + k];
+    v[k + 1] -= alpha;
+    for (int i = k + 1; i < m; ++i) vn += v[i] * v[i];
+    if (vn == 0.0) continue;
+    const double beta = 2.0 / vn;
+    // A <- (I - beta v v^T) A
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int i = k + 1; i < m; ++i) s += v[i] * A[(size_t)i * m + j];
+      s *= beta;
+      for (int i = k + 1; i < m; ++i) A[(size_t)i * m + j] -= s * v[i];
+    }
+    // A <- A (I - beta v v^T),  Q <- Q (I - beta v v^T)
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0, t = 0.0;
+      for (int j = k + 1; j < m; ++j) {
+        s += A[(size_t)i * m + j] * v[j];
+        t += Q[(size_t)i * m + j] * v[j];
+      }
+      s *= beta;
+      t *= beta;
+      for (int j = k + 1; j < m; ++j) {
+        A[(size_t)i * m + j] -= s * v[j];
+        Q[(size_t)i * m + j] -= t * v[j];
+      }
+    }
+    for (int i = k + 2; i < m; ++i) A[(size_t)i * m + k] = 0.0;
+  }
 }
 
 bool dense_solve(int n, std::vector<double> A, std::vector<double>& b) {

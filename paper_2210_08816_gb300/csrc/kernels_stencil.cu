@@ -596,6 +596,162 @@ __global__ void __launch_bounds__(256) k_correct(Geo<R> g, int N, const R* Y, co
   }
 }
 
+// FP32 forms of the divergence and the correction for nx % 4 == 0: a thread owns four x-consecutive cells
+// (16-byte loads and stores; the x-neighbour across the quad boundary comes from the next or previous lane)
+// and marches over kVZ z-planes, carrying the plane below in registers.  Block 32 x 8 (a warp is one
+// x-run of 128 cells).  Same arithmetic, element by element, as k_divergence / k_correct.
+constexpr int kVZ = 4;
+
+__device__ __forceinline__ float4 ldg4(const float* __restrict__ p, int o) {
+  return __ldg(reinterpret_cast<const float4*>(p + o));
+}
+__device__ __forceinline__ float4 ld4(const float* p, int o) { return *reinterpret_cast<const float4*>(p + o); }
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+__global__ void __launch_bounds__(256) k_divergence4(Geo<float> g, int N, const float* __restrict__ vel,
+                                                      float* __restrict__ rhs) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2], pl = nx * ny;
+  const int lane = threadIdx.x;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int k0 = blockIdx.z * kVZ, k1 = min(k0 + kVZ, nz);
+  const bool act = i0 < nx && j < ny;
+  const float* U = vel;
+  const float* V = vel + N;
+  const float* W = vel + 2 * N;
+  float4 rx = zero4();
+  float ry = 0.f;
+  if (act) {
+    rx = make_float4(__ldg(g.idx[0] + i0), __ldg(g.idx[0] + i0 + 1), __ldg(g.idx[0] + i0 + 2), __ldg(g.idx[0] + i0 + 3));
+    ry = __ldg(g.idx[1] + j);
+  }
+  const int ob = act ? (k0 * ny + j) * nx + i0 : 0;
+  float4 wlo = (act && k0 >= 1) ? ldg4(W, ob) : zero4();
+  for (int k = k0; k < k1; ++k) {
+    const int o = ob + (k - k0) * pl;
+    const float4 u = act ? ldg4(U, o) : zero4();
+    float un = __shfl_down_sync(0xffffffffu, u.x, 1);  // u on the face i0 + 4
+    if (lane == 31 && act && i0 + 4 < nx) un = __ldg(U + o + 4);
+    if (i0 + 4 >= nx) un = 0.f;
+    const float ux = (i0 == 0) ? 0.f : u.x;
+    if (!act) continue;
+    const float4 vlo = (j >= 1) ? ldg4(V, o) : zero4();
+    const float4 vhi = (j + 1 < ny) ? ldg4(V, o + nx) : zero4();
+    const float4 whi = (k + 1 < nz) ? ldg4(W, o + pl) : zero4();
+    const float rz = __ldg(g.idx[2] + k);
+    float4 r;
+    r.x = (u.y - ux) * rx.x + (vhi.x - vlo.x) * ry + (whi.x - wlo.x) * rz;
+    r.y = (u.z - u.y) * rx.y + (vhi.y - vlo.y) * ry + (whi.y - wlo.y) * rz;
+    r.z = (u.w - u.z) * rx.z + (vhi.z - vlo.z) * ry + (whi.z - wlo.z) * rz;
+    r.w = (un - u.w) * rx.w + (vhi.w - vlo.w) * ry + (whi.w - wlo.w) * rz;
+    *reinterpret_cast<float4*>(rhs + o) = r;
+    wlo = whi;
+  }
+}
+
+__device__ __forceinline__ void acc_sq(float& hi, float& lo, float r) {
+  const float p2 = r * r;
+  lo += fmaf(r, r, -p2);
+  two_sum_add(hi, lo, p2);
+}
+
+// out = alpha (Y - G phi) + beta v + gamma w on four cells; out may alias Y or w (read, then written,
+// by the same thread)
+__global__ void __launch_bounds__(256) k_correct4(Geo<float> g, int N, const float* Y, const float* __restrict__ phi,
+                                                   float alpha, const float* v, float beta, const float* w,
+                                                   float gamma, float* out, double* __restrict__ part) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2], pl = nx * ny;
+  const int lane = threadIdx.x;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int k0 = blockIdx.z * kVZ, k1 = min(k0 + kVZ, nz);
+  const bool act = i0 < nx && j < ny;
+  float4 cx = zero4();
+  float cy = 0.f;
+  if (act) {
+    cx = make_float4(__ldg(g.idc[0] + i0), __ldg(g.idc[0] + i0 + 1), __ldg(g.idc[0] + i0 + 2),
+                     __ldg(g.idc[0] + i0 + 3));
+    cy = __ldg(g.idc[1] + j);
+  }
+  const int ob = act ? (k0 * ny + j) * nx + i0 : 0;
+  float4 pzm = (act && k0 >= 1) ? ldg4(phi, ob - pl) : zero4();
+  float shi = 0.f, slo = 0.f;
+  for (int k = k0; k < k1; ++k) {
+    const int o = ob + (k - k0) * pl;
+    const float4 ph = act ? ldg4(phi, o) : zero4();
+    float pxm = __shfl_up_sync(0xffffffffu, ph.w, 1);  // phi in cell i0 - 1
+    if (lane == 0 && act && i0 > 0) pxm = __ldg(phi + o - 1);
+    if (!act) continue;
+    float4 G[3];
+    G[0] = make_float4((ph.x - pxm) * cx.x, (ph.y - ph.x) * cx.y, (ph.z - ph.y) * cx.z, (ph.w - ph.z) * cx.w);
+    if (j >= 1) {
+      const float4 pym = ldg4(phi, o - nx);
+      G[1] = make_float4((ph.x - pym.x) * cy, (ph.y - pym.y) * cy, (ph.z - pym.z) * cy, (ph.w - pym.w) * cy);
+    } else {
+      G[1] = zero4();
+    }
+    const float cz = __ldg(g.idc[2] + k);
+    G[2] = make_float4((ph.x - pzm.x) * cz, (ph.y - pzm.y) * cz, (ph.z - pzm.z) * cz, (ph.w - pzm.w) * cz);
+    pzm = ph;
+    const bool wall[3] = {false, j == 0, k == 0};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int od = d * N + o;
+      float4 r;
+      if (d < 3 && wall[d]) {
+        r = zero4();
+      } else {
+        const float4 y = ld4(Y, od);
+        const float4 gd = (d < 3) ? G[d] : zero4();
+        r = make_float4(alpha * (y.x - gd.x), alpha * (y.y - gd.y), alpha * (y.z - gd.z), alpha * (y.w - gd.w));
+        if (v) {
+          const float4 a = ld4(v, od);
+          r.x += beta * a.x; r.y += beta * a.y; r.z += beta * a.z; r.w += beta * a.w;
+        }
+        if (w) {
+          const float4 a = ld4(w, od);
+          r.x += gamma * a.x; r.y += gamma * a.y; r.z += gamma * a.z; r.w += gamma * a.w;
+        }
+        if (d == 0 && i0 == 0) r.x = 0.f;  // the x = 0 wall slot
+      }
+      *reinterpret_cast<float4*>(out + od) = r;
+      if (part) {
+        acc_sq(shi, slo, r.x);
+        acc_sq(shi, slo, r.y);
+        acc_sq(shi, slo, r.z);
+        acc_sq(shi, slo, r.w);
+      }
+    }
+  }
+  if (!part) return;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, shi, off), l2 = __shfl_down_sync(0xffffffffu, slo, off);
+    slo += l2;
+    two_sum_add(shi, slo, h2);
+  }
+  __shared__ double wpart[8];
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  if ((tid & 31) == 0) wpart[tid >> 5] = (double)shi + (double)slo;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += wpart[i];
+    part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = t;
+  }
+}
+
+inline bool quad_ok(const fv_grid_s* g, std::initializer_list<const void*> ptrs) {
+  if (g->nx % 4 != 0) return false;
+  for (const void* p : ptrs)
+    if (p && ((uintptr_t)p % 16) != 0) return false;
+  return true;
+}
+
+inline dim3 quad_grid(const fv_grid_s* g) {
+  return dim3((g->nx / 4 + 31) / 32, (g->ny + 7) / 8, (g->nz + kVZ - 1) / kVZ);
+}
+
 template <typename R>
 const Geo<R>& geo_of(const fv_grid_s* g);
 template <>
@@ -660,6 +816,13 @@ int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs) {
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_DIVERGENCE);
+  if constexpr (sizeof(R) == 4) {
+    if (quad_ok(g, {vel, rhs})) {
+      k_divergence4<<<quad_grid(g), dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, vel, rhs);
+      FV_CUDA(cudaGetLastError());
+      return FV_OK;
+    }
+  }
   k_divergence<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, vel, rhs);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
@@ -670,12 +833,21 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
                    const R* w, double gamma, R* out, int norm_slot) {
   dim3 grid, block;
   cell_grid(g, grid, block);
+  bool quad = false;
+  if constexpr (sizeof(R) == 4) quad = quad_ok(g, {Y, phi, v, w, out});
+  if (quad) grid = quad_grid(g);
   const int nblocks = (int)(grid.x * grid.y * grid.z);
   const bool want = norm_slot >= 0 && nblocks <= kPartialSlots - 64;
   {
     ProfScope ps(g, PROF_CORRECT);
-    k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w, (R)gamma,
-                                                out, want ? g->ws.partials : nullptr);
+    if constexpr (sizeof(R) == 4) {
+      if (quad)
+        k_correct4<<<grid, dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, Y, phi, (float)alpha, v, (float)beta, w,
+                                                        (float)gamma, out, want ? g->ws.partials : nullptr);
+    }
+    if (!quad)
+      k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w,
+                                                  (R)gamma, out, want ? g->ws.partials : nullptr);
     FV_CUDA(cudaGetLastError());
   }
   if (want) return launch_sum_partials(g, nblocks, norm_slot);

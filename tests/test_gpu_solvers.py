@@ -7,7 +7,11 @@
   Chebyshev-Arnoldi at Gr > 0 (both converged to 1e-9 residual: eigenvalues to 1e-8).
 * Mixed Arnoldi: leading eigenvalue within 1e-6 of the FP64 one; its Ritz vectors certified by the
   oracle's own FP64 residual ||P J x - lam x|| / (|lam| ||x||).
+* The 32^3, Gr = 1e5 workload: GPU Newton, then the four leading eigenvalues of both forms against
+  the oracle's stored ones (tests/golden/config0_eigs_32.txt).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -89,8 +93,9 @@ def test_newton_mixed_refines_to_fp64(fv):
     assert max(float(np.max(np.abs(a))) for a in r) <= 1e-9 * scale
 
 
-def test_newton_32cube_uniform_config(fv):
-    """32^3 uniform, Pr = 0.71, Gr = 1e5 (continuation from 1.25e4), inner solves to 1e-10."""
+@pytest.fixture(scope="module")
+def cube32(fv):
+    """32^3 uniform, Pr = 0.71, Gr = 1e5: GPU Newton from conduction (continuation from 1.25e4)."""
     shape, Gr = (32, 32, 32), 1.0e5
     og = D.Grid(*shape, stretch=0.0, Pr=PR)
     g = fv.Grid(*shape, stretch=0.0, Pr=PR)
@@ -98,6 +103,12 @@ def test_newton_32cube_uniform_config(fv):
     o = fv.fv_newton_default_opts()
     o.gr_start, o.gr_ratio = 1.25e4, 2.0
     st, rep = fv.newton_steady(g, Gr, q, o)
+    return og, g, Gr, q, st, rep
+
+
+def test_newton_32cube_uniform_config(fv, cube32):
+    """32^3 uniform, Pr = 0.71, Gr = 1e5 (continuation from 1.25e4), inner solves to 1e-10."""
+    og, g, Gr, q, st, rep = cube32
     assert st == fv.FV_OK
     got = host(q, og.shape)
     P = Projector(og)
@@ -105,6 +116,30 @@ def test_newton_32cube_uniform_config(fv):
     assert max(float(np.max(np.abs(a))) for a in r) <= 1e-9 * rep.residual0
     assert max(DG.symmetry_measures(og, got[3])) <= 1e-9
     assert DG.nusselt_hot(og, got[3]) < -1.0
+
+
+def _golden_eigs(name):
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", name))
+            if ln.strip() and not ln.startswith("#")]
+    return np.array([float(a) + 1j * float(b) for a, b in rows])
+
+
+def test_arnoldi_32cube_matches_stored_oracle_eigenvalues(fv, cube32):
+    """The 32^3 Gr = 1e5 workload: four leading eigenvalues (k = 4, m = 20) by the FP64 and the mixed
+    GPU forms against the oracle's, stored by tests/golden/make_config0_eigs.py (tol 1e-9)."""
+    og, g, Gr, q, st, rep = cube32
+    assert st == fv.FV_OK
+    ref = _golden_eigs("config0_eigs_32.txt")
+    o = fv.fv_arnoldi_default_opts()
+    o.tol = 1e-9
+    st, lam, r64 = fv.arnoldi_leading(g, 4, Gr, q, o)
+    assert st == fv.FV_OK
+    assert len(lam) == len(ref) and np.allclose(np.array(lam), ref, rtol=1e-8, atol=0), (lam, ref)
+    o.precision = fv.FV_FP32
+    o.tol = 1e-6
+    st, lam32, r32 = fv.arnoldi_leading(g, 4, Gr, q, o)
+    assert st == fv.FV_OK
+    assert np.allclose(np.array(lam32[:len(ref)]), ref, rtol=1e-6, atol=0), (lam32, ref)
 
 
 def test_arnoldi_fp64_gr0_closed_form(fv):
