@@ -273,7 +273,7 @@ def gpu_arm(args, ws, rank, local):
     else:
         bytes_per = {"stencil": 12 * N * 4, "correct": 17 * N * 4, "divergence": 4 * N * 4}.get(dom, 2 * 4 * N * 4)
         achieved = bytes_per / (per_launch_ms * 1e-3) / 1e9
-        names = {"stencil": "k_stencil_z<float,1> (J.v)", "correct": "k_correct<float>"}
+        names = {"stencil": "k_stencil_z<float,1> (J.v)", "correct": "k_correct4", "divergence": "k_divergence4"}
         roof = {"kernel": names.get(dom, dom), "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "peak_source": hbm_src}
         traffic_bytes = bytes_per
@@ -414,7 +414,11 @@ def eigen_leg(fv, device):
         st, l, r = fv.arnoldi_leading(g, 4, Gr, q, a)
         torch.cuda.synchronize()
         out[name] = {"seconds": round(time.time() - t0, 3), "status": st, "matvecs": r.matvecs,
-                     "restarts": r.restarts, "lambda1": [l[0].real, l[0].imag] if l else None}
+                     "cycles": r.restarts, "degrees": list(r.degrees[:r.restarts]),
+                     "max_residual": max(r.residual[i] for i in range(r.nconv)) if r.nconv else None,
+                     "lambda1": [l[0].real, l[0].imag] if l else None}
+        if prec == fv.FV_FP32:
+            out[name].update(fp32_cycles=r.restarts_low, fp32_matvecs=r.matvecs_low)
         lam[name] = l[0] if l else None
     if lam.get("fp64") is not None and lam.get("mixed") is not None:
         out["lambda1_rel_diff"] = abs(lam["mixed"] - lam["fp64"]) / abs(lam["fp64"])

@@ -183,7 +183,8 @@ typedef struct {
     int precision;        /* FV_FP64, or FV_FP32: a phase with FP32 Krylov vectors and
                              J.v + projection (FP64 Rayleigh-Ritz matrix, Gram-Schmidt
                              coefficients and inner products) down to residual low_tol, then
-                             FP64 cycles started from its Ritz vectors refine to tol */
+                             FP64 cycles started from its Ritz vectors, with the polynomial
+                             degree capped at max_degree / 8, refine to tol */
     int m;                /* Krylov subspace dimension per cycle */
     double tol;           /* stop when every wanted Ritz pair has
                              ||A x - lam x|| <= tol |lam| ||x|| (true residual, FP64 reductions) */
@@ -193,7 +194,7 @@ typedef struct {
     int guard;            /* extra Ritz values kept outside the filter's ellipse (default 2) */
     unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected */
     double sigma;         /* shift of the gradient complement; 0 = automatic */
-    double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-4); the phase
+    double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-3); the phase
                              also ends once its largest residual has not halved in 3 cycles */
     int low_max_restarts; /* FV_FP32: cycle cap of the FP32 phase (default 20) */
 } fv_arnoldi_opts;

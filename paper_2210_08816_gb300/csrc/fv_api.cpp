@@ -724,7 +724,7 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->guard = 2;
   o->seed = 1;
   o->sigma = 0.0;
-  o->low_tol = 1e-4;
+  o->low_tol = 1e-3;
   o->low_max_restarts = 20;
 }
 
@@ -1294,8 +1294,13 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   fv_arnoldi_report r2;
   std::memset(&r2, 0, sizeof(r2));
   if (vecs_out) FV_TRY(X64.alloc((size_t)(k + 1) * n));
+  // the FP64 cycles start from vectors already accurate to the FP32 floor and need little gain: their
+  // polynomial degree is capped at an eighth of the FP32 phase's (each FP64 J.v + projection costs many
+  // FP32 ones on this part)
   fv_arnoldi_opts o2 = o;
   o2.precision = FV_FP64;
+  o2.max_degree = std::max(o.min_degree, o.max_degree / 8);
+  carry.filt.deg = std::min(carry.filt.deg, o2.max_degree);
   const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry);
   if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
     for (int i = 0; i < r2.nconv; ++i)
