@@ -137,6 +137,16 @@ int fv_dot_noalloc(int prec, long long n, const void* a, const void* b, double* 
 
 /* y <- alpha x + beta y over 4N elements (coefficients applied in FP64). */
 int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y);
+/* out = L^-1 in, where L is the diffusion part of J (Eqs. 1-2 with homogeneous wall data): per
+ * velocity component the Laplacian with no-slip walls, for T the Laplacian / Pr with T = 0 at the
+ * x-walls (Eq. 4) and zero flux at the others (Eqs. 5-6).  Separable on the tensor-product grid, so
+ * it is inverted directly by fast diagonalisation (six dense passes per field; nothing iterates).
+ * The building block of newton_steady's optional preconditioner; the paper names no preconditioner
+ * (Section 1 methods paragraph).  in, out: device, 4N elements of the precision `prec`, API layout;
+ * the wall slots of the face fields must hold zero in `in` and hold zero in `out`; in and out may
+ * alias.  Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM (workspace). */
+int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out);
+
 /* Element-type conversion of a state: FP64 -> FP32 (to_fp32 = 1) or back. */
 int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst);
 
@@ -152,6 +162,9 @@ typedef struct {
     int gmres_m;          /* restart length of the GMRES fallback */
     double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr */
     double gr_ratio;      /* continuation factor per step (> 1) */
+    int precond;          /* 0 (default): none; 1: right preconditioner M^-1 = P L^-1, L the
+                             diffusion operator of J inverted by fast diagonalisation (see
+                             fv_diffusion_solve) */
 } fv_newton_opts;
 
 typedef struct {

@@ -92,7 +92,67 @@ static std::vector<double> tanh_faces(int n, double s) {
 struct AxisHost {
   int n;
   std::vector<double> idx, idc, wl, wr, lam, Einv, E;
+  // diffusion operators of the Newton preconditioner: cell-centred with Dirichlet walls half a cell away
+  // (transverse velocities, T along x) and face-centred with Dirichlet walls (a velocity along its own
+  // axis; mode 0 is a dummy that maps the wall slot 0 to itself)
+  std::vector<double> cd_lam, cd_Einv, cd_E, fd_lam, fd_Einv, fd_E;
 };
+
+// Generalised eigen-decomposition of L = W^-1 K (K symmetric tridiagonal: diagonal kd, off-diagonal ko;
+// W > 0 diagonal) through B = W^-1/2 K W^-1/2:  L = E diag(lam) Einv, E = W^-1/2 Q, Einv = Q^T W^1/2.
+// The m x m result is written at offset `o` of n x n matrices (rows/columns o .. o+m-1).
+static int tridiag_operator(int m, const std::vector<double>& kd, const std::vector<double>& ko,
+                            const std::vector<double>& W, int n, int o, std::vector<double>& lam,
+                            std::vector<double>& Einv, std::vector<double>& E) {
+  if (m <= 0) return FV_OK;
+  std::vector<double> d(m), e(std::max(m - 1, 1), 0.0), Q;
+  for (int i = 0; i < m; ++i) d[i] = kd[i] / W[i];
+  for (int i = 0; i + 1 < m; ++i) e[i] = ko[i] / std::sqrt(W[i] * W[i + 1]);
+  if (!tridiag_eig(m, d, e, Q)) return invalid("tridiagonal eigensolver did not converge");
+  for (int k = 0; k < m; ++k) {
+    lam[o + k] = d[k];
+    for (int i = 0; i < m; ++i) {
+      const double qv = Q[(size_t)i * m + k];
+      E[(size_t)(o + i) * n + (o + k)] = qv / std::sqrt(W[i]);
+      Einv[(size_t)(o + k) * n + (o + i)] = qv * std::sqrt(W[i]);
+    }
+  }
+  return FV_OK;
+}
+
+// The two Dirichlet diffusion operators of one axis (same flux form as the stencils' Laplacian).
+static int build_dirichlet_ops(AxisHost& a) {
+  const int n = a.n;
+  // cell-centred: (L u)_i = [ (u_{i+1} - u_i) idc[i+1] - (u_i - u_{i-1}) idc[i] ] idx[i], u_{-1} = u_n = 0,
+  // idc[0] = 2 / dx_0 and idc[n] = 2 / dx_{n-1} (walls half a cell away)
+  std::vector<double> kd(n), ko(std::max(n - 1, 1), 0.0), W(n);
+  for (int i = 0; i < n; ++i) {
+    kd[i] = -(a.idc[i] + a.idc[i + 1]);
+    if (i + 1 < n) ko[i] = a.idc[i + 1];
+    W[i] = 1.0 / a.idx[i];
+  }
+  a.cd_lam.assign(n, 0.0);
+  a.cd_Einv.assign((size_t)n * n, 0.0);
+  a.cd_E.assign((size_t)n * n, 0.0);
+  FV_TRY(tridiag_operator(n, kd, ko, W, n, 0, a.cd_lam, a.cd_Einv, a.cd_E));
+  // face-centred on faces p = 1 .. n-1: (L u)_p = [ (u_{p+1} - u_p) idx[p] - (u_p - u_{p-1}) idx[p-1] ] idc[p],
+  // u_0 = u_n = 0; control-volume width 1 / idc[p]
+  const int mf = n - 1;
+  std::vector<double> fd(std::max(mf, 1)), fo(std::max(mf, 1), 0.0), FW(std::max(mf, 1));
+  for (int k = 0; k < mf; ++k) {
+    const int p = k + 1;
+    fd[k] = -(a.idx[p] + a.idx[p - 1]);
+    if (k + 1 < mf) fo[k] = a.idx[p];
+    FW[k] = 1.0 / a.idc[p];
+  }
+  a.fd_lam.assign(n, 0.0);
+  a.fd_Einv.assign((size_t)n * n, 0.0);
+  a.fd_E.assign((size_t)n * n, 0.0);
+  a.fd_lam[0] = -1.0;  // dummy mode of the wall slot (its input is zero)
+  a.fd_E[0] = 1.0;
+  a.fd_Einv[0] = 1.0;
+  return tridiag_operator(mf, fd, fo, FW, n, 1, a.fd_lam, a.fd_Einv, a.fd_E);
+}
 
 static int build_axis(const std::vector<double>& xf, AxisHost& a) {
   const int n = (int)xf.size() - 1;
@@ -141,13 +201,14 @@ static int build_axis(const std::vector<double>& xf, AxisHost& a) {
       a.Einv[(size_t)m * n + i] = qv * std::sqrt(dx[i]);
     }
   }
-  return FV_OK;
+  return build_dirichlet_ops(a);
 }
 
 template <typename R>
-static int upload_axes(fv_grid_s* g, const AxisHost* ax, int which, Geo<R>& geo, FdmDev<R>& fdm) {
+static int upload_axes(fv_grid_s* g, const AxisHost* ax, int which, Geo<R>& geo, FdmDev<R>& fdm, FdmDev<R>& cd,
+                       FdmDev<R>& fd) {
   size_t total = 0;
-  for (int d = 0; d < 3; ++d) total += 4 * (size_t)(ax[d].n + 1) + ax[d].n + 2 * (size_t)ax[d].n * ax[d].n;
+  for (int d = 0; d < 3; ++d) total += 4 * (size_t)(ax[d].n + 1) + 3 * ((size_t)ax[d].n + 2 * (size_t)ax[d].n * ax[d].n);
   std::vector<R> h(total);
   std::vector<size_t> off;
   size_t o = 0;
@@ -163,6 +224,12 @@ static int upload_axes(fv_grid_s* g, const AxisHost* ax, int which, Geo<R>& geo,
     put(ax[d].lam);
     put(ax[d].Einv);
     put(ax[d].E);
+    put(ax[d].cd_lam);
+    put(ax[d].cd_Einv);
+    put(ax[d].cd_E);
+    put(ax[d].fd_lam);
+    put(ax[d].fd_Einv);
+    put(ax[d].fd_E);
   }
   void* buf = nullptr;
   cudaError_t e = cudaMalloc(&buf, total * sizeof(R));
@@ -175,13 +242,20 @@ static int upload_axes(fv_grid_s* g, const AxisHost* ax, int which, Geo<R>& geo,
   const R* base = (const R*)buf;
   for (int d = 0; d < 3; ++d) {
     geo.n[d] = ax[d].n;
-    geo.idx[d] = base + off[7 * d + 0];
-    geo.idc[d] = base + off[7 * d + 1];
-    geo.wl[d] = base + off[7 * d + 2];
-    geo.wr[d] = base + off[7 * d + 3];
-    fdm.lam[d] = base + off[7 * d + 4];
-    fdm.Einv[d] = base + off[7 * d + 5];
-    fdm.E[d] = base + off[7 * d + 6];
+    const size_t* od = off.data() + 13 * d;
+    geo.idx[d] = base + od[0];
+    geo.idc[d] = base + od[1];
+    geo.wl[d] = base + od[2];
+    geo.wr[d] = base + od[3];
+    fdm.lam[d] = base + od[4];
+    fdm.Einv[d] = base + od[5];
+    fdm.E[d] = base + od[6];
+    cd.lam[d] = base + od[7];
+    cd.Einv[d] = base + od[8];
+    cd.E[d] = base + od[9];
+    fd.lam[d] = base + od[10];
+    fd.Einv[d] = base + od[11];
+    fd.E[d] = base + od[12];
   }
   return FV_OK;
 }
@@ -307,15 +381,41 @@ struct Vec {
   }
 };
 
+// ------------------------------------------------------------------ Newton preconditioner
+// out = L^-1 in, field by field (the diffusion operator of J with homogeneous wall data); in and out
+// may alias.
+template <typename R>
+static int diffusion_solve(fv_grid_s* g, const R* in, R* out) {
+  FV_TRY(ensure_ws<R>(g));
+  R* tmp = (R*)g->ws.t0[prec_index<R>()];
+  for (int f = 0; f < 4; ++f) FV_TRY(launch_field_solve<R>(g, f, in + (size_t)f * g->N, out + (size_t)f * g->N, tmp));
+  return FV_OK;
+}
+
+// Right preconditioner M^-1 = P L^-1 (the diffusion part of J inverted, then projected): it removes
+// the stiff diffusion eigenvalues (up to ~12 / h_min^2) from P J M^-1, but P and L do not commute at
+// no-slip walls, so P J M^-1 is not a compact perturbation of P there.
+template <typename R>
+static int apply_precond(fv_grid_s* g, const R* in, R* out) {
+  FV_TRY(diffusion_solve<R>(g, in, out));
+  return project_inplace<R>(g, out, 1, 0.0, nullptr, nullptr);
+}
+
 // ------------------------------------------------------------------ BiCGstab(2) and GMRES
+// y = A x = P (J - sigma) x + sigma x, or A M^-1 x when `pre` (a 4N scratch vector) is set.
 template <typename R>
 struct Operator {
   fv_grid_s* g;
   double Gr, sigma;
   const R* q;
   long long* matvecs;
+  R* pre = nullptr;
   int apply(const R* x, R* y) {
     ++*matvecs;
+    if (pre) {
+      FV_TRY(apply_precond<R>(g, x, pre));
+      return jvp_project<R>(g, Gr, sigma, q, pre, y);
+    }
     return jvp_project<R>(g, Gr, sigma, q, x, y);
   }
 };
@@ -545,8 +645,8 @@ int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out) {
       g->min_width[d] = mw;
     }
   }
-  if (st == FV_OK) st = upload_axes<double>(g, ax, 0, g->geo64, g->fdm64);
-  if (st == FV_OK) st = upload_axes<float>(g, ax, 1, g->geo32, g->fdm32);
+  if (st == FV_OK) st = upload_axes<double>(g, ax, 0, g->geo64, g->fdm64, g->cd64, g->fd64);
+  if (st == FV_OK) st = upload_axes<float>(g, ax, 1, g->geo32, g->fdm32, g->cd32, g->fd32);
   if (st == FV_OK && tc_eligible(g)) {
     std::vector<double> idx[3] = {ax[0].idx, ax[1].idx, ax[2].idx}, idc[3] = {ax[0].idc, ax[1].idc, ax[2].idc};
     if (tc_setup(g, idx, idc) != FV_OK) {  // keep the SIMT passes
@@ -649,6 +749,13 @@ int fv_project(fv_grid g, int prec, void* v, int max_it, double tol, int* iters,
   return invalid("precision must be FV_FP64 or FV_FP32");
 }
 
+int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out) {
+  if (!g || !in || !out) return invalid("null argument");
+  if (prec == FV_FP64) return diffusion_solve<double>(g, (const double*)in, (double*)out);
+  if (prec == FV_FP32) return diffusion_solve<float>(g, (const float*)in, (float*)out);
+  return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
 int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v, void* out) {
   if (!g || !q || !v || !out) return invalid("null argument");
   if (out == q || out == v) return invalid("out must not alias q or v");
@@ -711,6 +818,7 @@ void fv_newton_default_opts(fv_newton_opts* o) {
   o->gmres_m = 30;
   o->gr_start = 0.0;
   o->gr_ratio = 2.0;
+  o->precond = 0;
 }
 
 void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
@@ -749,6 +857,8 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
   FV_TRY(work.alloc(7 * n));
   FV_TRY(basis.alloc((size_t)(o.gmres_m + 1) * n));
   FV_TRY(w.alloc(n));
+  DevBuf<R> pre;
+  if (o.precond) FV_TRY(pre.alloc(n));
   const double sigma = g->sigma_default;
   const double ktol = mixed ? std::max(o.krylov_tol, 1e-5) : o.krylov_tol;
   double r0 = -1.0;
@@ -788,6 +898,7 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
     FV_TRY(VR.lin(b, {{-1.0, b}}));
     long long mv = 0;
     Operator<R> A{g, Gr, sigma, qop, &mv};
+    A.pre = o.precond ? pre.p : nullptr;
     SolveInfo info;
     FV_TRY(bicgstab2<R>(A, b, x.p, ktol, o.max_matvec, work.p, info));
     if (info.status != FV_OK && (info.breakdown || info.stalled)) {
@@ -796,6 +907,11 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
       rep->gmres_fallbacks += 1;
     }
     rep->matvecs += (int)mv;
+    if (o.precond) {  // right preconditioning: delta = M^-1 y
+      FV_TRY(apply_precond<R>(g, x.p, pre.p));
+      Vec<R> VP{g, n};
+      FV_TRY(VP.copy(x.p, pre.p));
+    }
     // delta -> FP64, re-projected in FP64 so that q stays divergence free to FP64 accuracy
     if (mixed) {
       FV_TRY(launch_convert(g, n, (const float*)x.p, d64.p));
@@ -819,7 +935,8 @@ extern "C" int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_new
   else
     fv_newton_default_opts(&o);
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
-  if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200) return invalid("bad Newton options");
+  if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200 || o.precond < 0 || o.precond > 1)
+    return invalid("bad Newton options");
   fv_newton_report rep;
   std::memset(&rep, 0, sizeof(rep));
   std::vector<double> ladder;
@@ -1294,13 +1411,8 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   fv_arnoldi_report r2;
   std::memset(&r2, 0, sizeof(r2));
   if (vecs_out) FV_TRY(X64.alloc((size_t)(k + 1) * n));
-  // the FP64 cycles start from vectors already accurate to the FP32 floor and need little gain: their
-  // polynomial degree is capped at an eighth of the FP32 phase's (each FP64 J.v + projection costs many
-  // FP32 ones on this part)
   fv_arnoldi_opts o2 = o;
   o2.precision = FV_FP64;
-  o2.max_degree = std::max(o.min_degree, o.max_degree / 8);
-  carry.filt.deg = std::min(carry.filt.deg, o2.max_degree);
   const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry);
   if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
     for (int i = 0; i < r2.nconv; ++i)

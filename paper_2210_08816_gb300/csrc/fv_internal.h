@@ -83,6 +83,9 @@ struct fv_grid_s {
   fv::Geo<float> geo32;
   fv::FdmDev<double> fdm64;
   fv::FdmDev<float> fdm32;
+  // Dirichlet diffusion operators (cell-centred, face-centred) of the Newton preconditioner
+  fv::FdmDev<double> cd64, fd64;
+  fv::FdmDev<float> cd32, fd32;
   fv::Workspace ws;
   double sigma_default;
   double min_width[3];
@@ -141,6 +144,10 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>
 int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp);
+// out = L_f^-1 in for one field f (0..2 velocity with no-slip walls, 3 temperature with Eqs. 4-6 homogeneous
+// and the 1/Pr factor): the diffusion operator of J, inverted by fast diagonalisation (6 passes).
+template <typename R>
+int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp);
 
 // BLAS-1 and reductions (kernels_blas.cu).  Results land in g->ws.scalars[slot...].
 template <typename R>

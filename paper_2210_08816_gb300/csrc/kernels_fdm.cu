@@ -31,8 +31,10 @@ struct TileCfg<double> {
 
 struct PassArgs {
   int P, nm, K;          // rows (a*b), modes, contraction length
-  int scale;             // third forward pass: divide by lam_z[m] + lam_y[p / nb] + lam_x[p % nb]
+  int scale;             // third forward pass: multiply by sfac / (lam_z[m] + lam_y[p / nb] + lam_x[p % nb])
   int nb;
+  int zero_mode;         // the (0,0,0) mode is the null space (Neumann): set it to zero
+  double sfac;
 };
 
 template <typename R>
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(256) k_transform(PassArgs t, const R* __restri
       R val = acc[i][j];
       if (t.scale) {
         const int a = p / t.nb, b = p - a * t.nb;
-        val = (m == 0 && a == 0 && b == 0) ? R(0) : val / (lz[m] + ly[a] + lx[b]);
+        val = (t.zero_mode && m == 0 && a == 0 && b == 0) ? R(0) : R(t.sfac) * val / (lz[m] + ly[a] + lx[b]);
       }
       out[(long long)m * t.P + p] = val;
     }
@@ -105,23 +107,44 @@ const FdmDev<double>& fdm_of<double>(const fv_grid_s* g) { return g->fdm64; }
 template <>
 const FdmDev<float>& fdm_of<float>(const fv_grid_s* g) { return g->fdm32; }
 
-// in[a][b][k] -> out[m][a][b] with M (nm x K)
+// in[a][b][k] -> out[m][a][b] with M (nm x K); a scaled pass divides by the eigenvalue sums of lam[0..2]
 template <typename R>
-int pass(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale) {
+int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale,
+             const R* const lam[3], bool zero_mode, double sfac) {
   using T = TileCfg<R>;
-  const FdmDev<R>& f = fdm_of<R>(g);
   PassArgs t{};
   t.P = na * nb;
   t.nm = K;
   t.K = K;
   t.scale = scale ? 1 : 0;
   t.nb = nb;
+  t.zero_mode = zero_mode ? 1 : 0;
+  t.sfac = sfac;
   dim3 grid((t.P + T::BM - 1) / T::BM, (t.nm + T::BN - 1) / T::BN, 1);
   ProfScope ps(g, PROF_TRANSFORM);
-  k_transform<R><<<grid, 256, 0, g->stream>>>(t, in, M, out, f.lam[0], f.lam[1], f.lam[2]);
+  k_transform<R><<<grid, 256, 0, g->stream>>>(t, in, M, out, lam[0], lam[1], lam[2]);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
+
+template <typename R>
+int pass(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale) {
+  const FdmDev<R>& f = fdm_of<R>(g);
+  return pass_ops<R>(g, M, na, nb, K, in, out, scale, f.lam, true, 1.0);
+}
+
+template <typename R>
+const FdmDev<R>& cd_of(const fv_grid_s* g);
+template <>
+const FdmDev<double>& cd_of<double>(const fv_grid_s* g) { return g->cd64; }
+template <>
+const FdmDev<float>& cd_of<float>(const fv_grid_s* g) { return g->cd32; }
+template <typename R>
+const FdmDev<R>& fd_of(const fv_grid_s* g);
+template <>
+const FdmDev<double>& fd_of<double>(const fv_grid_s* g) { return g->fd64; }
+template <>
+const FdmDev<float>& fd_of<float>(const fv_grid_s* g) { return g->fd32; }
 
 }  // namespace
 
@@ -164,5 +187,34 @@ int launch_poisson<float>(const fv_grid_s* g, const float* rhs, float* phi, floa
 }
 
 template int launch_poisson<double>(const fv_grid_s*, const double*, double*, double*);
+
+// Diffusion operator of one field, L_f = s_f (L_x (+) L_y (+) L_z), inverted like the pressure operator:
+// velocity component c uses the face-centred Dirichlet operator along its own axis and the cell-centred
+// Dirichlet operator across (no-slip walls half a cell away); temperature uses cell-centred Dirichlet in
+// x (Eq. 4, homogeneous) and the Neumann operator in y and z (Eqs. 5-6), with s_T = 1/Pr.  No zero mode.
+// in and out may alias; tmp may not.
+template <typename R>
+int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp) {
+  const FdmDev<R>* op[3];
+  for (int d = 0; d < 3; ++d) {
+    if (field < 3)
+      op[d] = (d == field) ? &fd_of<R>(g) : &cd_of<R>(g);
+    else
+      op[d] = (d == 0) ? &cd_of<R>(g) : &fdm_of<R>(g);
+  }
+  const R* lam[3] = {op[0]->lam[0], op[1]->lam[1], op[2]->lam[2]};
+  const double sfac = (field == 3) ? g->Pr : 1.0;
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  FV_TRY(pass_ops<R>(g, op[0]->Einv[0], nz, ny, nx, in, tmp, false, lam, false, 1.0));
+  FV_TRY(pass_ops<R>(g, op[1]->Einv[1], nx, nz, ny, tmp, out, false, lam, false, 1.0));
+  FV_TRY(pass_ops<R>(g, op[2]->Einv[2], ny, nx, nz, out, tmp, true, lam, false, sfac));
+  FV_TRY(pass_ops<R>(g, op[0]->E[0], nz, ny, nx, tmp, out, false, lam, false, 1.0));
+  FV_TRY(pass_ops<R>(g, op[1]->E[1], nx, nz, ny, out, tmp, false, lam, false, 1.0));
+  FV_TRY(pass_ops<R>(g, op[2]->E[2], ny, nx, nz, tmp, out, false, lam, false, 1.0));
+  return FV_OK;
+}
+
+template int launch_field_solve<double>(const fv_grid_s*, int, const double*, double*, double*);
+template int launch_field_solve<float>(const fv_grid_s*, int, const float*, float*, float*);
 
 }  // namespace fv

@@ -32,7 +32,7 @@ class fv_grid_desc(C.Structure):
 class fv_newton_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("krylov_tol", C.c_double),
                 ("max_newton", C.c_int), ("max_matvec", C.c_int), ("gmres_m", C.c_int),
-                ("gr_start", C.c_double), ("gr_ratio", C.c_double)]
+                ("gr_start", C.c_double), ("gr_ratio", C.c_double), ("precond", C.c_int)]
 
 
 class fv_newton_report(C.Structure):
@@ -80,6 +80,7 @@ def lib():
             "fv_dot_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp]),
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
             "fv_convert": (i, [vp, i, vp, vp]),
+            "fv_diffusion_solve": (i, [vp, i, vp, vp]),
             "fv_newton_default_opts": (None, [C.POINTER(fv_newton_opts)]),
             "newton_steady": (i, [vp, d, vp, C.POINTER(fv_newton_opts), C.POINTER(fv_newton_report)]),
             "fv_arnoldi_default_opts": (None, [C.POINTER(fv_arnoldi_opts)]),
@@ -99,7 +100,8 @@ def lib():
 
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
-            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_newton_default_opts",
+            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve",
+            "fv_newton_default_opts",
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
 
@@ -194,6 +196,14 @@ def fv_project(g: Grid, prec, v, max_it=1, tol=0.0, want_div=False):
     _check(lib().fv_project(g.h, prec, _ptr(v, g.dtype(prec), g.n, "v"), int(max_it), float(tol), C.byref(it),
                             C.byref(dv) if want_div else None), "fv_project")
     return it.value, (dv.value if want_div else None)
+
+
+def fv_diffusion_solve(g: Grid, prec, x, out):
+    """out = L^-1 x (the diffusion operator of J, per field); x and out may be the same tensor."""
+    dt = g.dtype(prec)
+    _check(lib().fv_diffusion_solve(g.h, prec, _ptr(x, dt, g.n, "x"), _ptr(out, dt, g.n, "out")),
+           "fv_diffusion_solve")
+    return out
 
 
 def fv_jvp_project(g: Grid, prec, Gr, sigma, q, v, out):

@@ -209,3 +209,30 @@ def test_fused_recurrence_step(fv, prec_name):
     assert rel(got, ref) <= tol
     ref_n2 = sum(float(np.sum(a * a)) for a in got)   # the fused norm is that of the stored result
     assert nrm == pytest.approx(ref_n2, rel=1e-12)
+
+
+@pytest.mark.parametrize("shape,stretch", [((17, 13, 11), 1.5), ((16, 12, 10), 0.0), ((2, 2, 3), 0.0)])
+def test_diffusion_solve_inverts_the_oracle_diffusion(fv, shape, stretch):
+    """fv_diffusion_solve (L^-1 of the Newton preconditioner): the oracle's diffusion operator with
+    homogeneous wall data maps the FP64 output back onto the input (1e-10: the check goes through L,
+    whose condition number here is ~1e4); the FP32 output matches the FP64 one within the projection's
+    FP32 bound."""
+    og = D.Grid(*shape, stretch=stretch, Pr=PR)
+    g = fv.Grid(*shape, stretch=stretch, Pr=PR)
+    x = D.to_api(og, D.from_api(og, seeded.normal_fields(41, og.shape)))  # wall slots zero
+    x64 = dev(x, torch.float64)
+    out64 = torch.empty_like(x64)
+    fv.fv_diffusion_solve(g, fv.FV_FP64, x64, out64)
+    got = host(out64, og.shape)
+    back = D.diffusion(og, D.from_api(og, got), 0.0)
+    full = D.from_api(og, x)
+    interior = [full[0][:, :, 1:-1], full[1][:, 1:-1, :], full[2][1:-1, :, :], full[3]]
+    assert rel(back, interior) <= 1e-10
+    for c in range(3):  # wall slots stay zero
+        assert np.all(np.take(got[c], 0, axis=2 - c) == 0.0)
+    x32 = dev(x, torch.float32)
+    out32 = torch.empty_like(x32)
+    fv.fv_diffusion_solve(g, fv.FV_FP32, x32, out32)
+    assert rel(host(out32, og.shape), got) <= TOL32_PROJ
+    fv.fv_diffusion_solve(g, fv.FV_FP64, x64, x64)  # in place
+    assert rel(host(x64, og.shape), got) <= 1e-14

@@ -1,6 +1,6 @@
 """GPU Newton and Chebyshev-Arnoldi drivers (through the C-ABI) against the oracle.
 
-* FP64 Newton reaches the oracle's steady state (both solve P F = 0 to round-off; the states agree
+* FP64 Newton, with and without its optional diffusion preconditioner, reaches the oracle's steady state (both solve P F = 0 to round-off; the states agree
   to 1e-9 in max-norm, the residual tolerance divided by the smallest eigenvalue magnitude).
 * Mixed Newton (FP32 Krylov, FP64 residual) refines to the FP64 state within 1e-8 max-norm.
 * FP64 Arnoldi: Gr = 0 closed-form temperature spectrum, and agreement with the oracle's
@@ -53,7 +53,10 @@ def conduction_api(og):
     return D.to_api(og, D.conduction_state(og))
 
 
-def test_newton_fp64_matches_oracle(fv):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_newton_fp64_matches_oracle(fv, precond):
+    """With and without the diffusion preconditioner: the same steady state as the (unpreconditioned)
+    oracle Newton."""
     shape, Gr = (10, 8, 6), 1.2e4
     og = D.Grid(*shape, stretch=1.5, Pr=PR)
     q_ref, rep_ref = SV.newton_steady(og, Gr, D.conduction_state(og), tol=1e-11)
@@ -62,6 +65,7 @@ def test_newton_fp64_matches_oracle(fv):
     q = dev(conduction_api(og))
     o = fv.fv_newton_default_opts()
     o.tol = 1e-11
+    o.precond = precond
     st, rep = fv.newton_steady(g, Gr, q, o)
     assert st == fv.FV_OK, rep.history[:rep.newton_steps + 1]
     got = host(q, og.shape)
