@@ -156,15 +156,18 @@ typedef struct {
                              J.v+projection in FP32; residual, updates and inner
                              products FP64 (the outer loop refines to FP64). */
     double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) */
-    double krylov_tol;    /* relative residual of each inner solve */
+    double krylov_tol;    /* relative residual of each inner solve (forcing = 0), or its floor */
     int max_newton;       /* Newton steps */
     int max_matvec;       /* J.v+projections per inner solve */
     int gmres_m;          /* restart length of the GMRES fallback */
     double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr */
     double gr_ratio;      /* continuation factor per step (> 1) */
-    int precond;          /* 0 (default): none; 1: right preconditioner M^-1 = P L^-1, L the
-                             diffusion operator of J inverted by fast diagonalisation (see
-                             fv_diffusion_solve) */
+    int precond;          /* 1 (default): right preconditioner M^-1 = P L^-1, L the diffusion
+                             operator of J inverted by fast diagonalisation (see
+                             fv_diffusion_solve): inner iteration counts stay nearly flat as the
+                             grid is refined; 0: none */
+    int forcing;          /* 1 (default): inner tolerance by Eisenstat-Walker, 0.9 (r_k/r_{k-1})^2
+                             within [max(krylov_tol, target / (2 r_k)), 1e-2]; 0: krylov_tol */
 } fv_newton_opts;
 
 typedef struct {

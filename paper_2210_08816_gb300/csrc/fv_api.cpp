@@ -818,7 +818,8 @@ void fv_newton_default_opts(fv_newton_opts* o) {
   o->gmres_m = 30;
   o->gr_start = 0.0;
   o->gr_ratio = 2.0;
-  o->precond = 0;
+  o->precond = 1;
+  o->forcing = 1;
 }
 
 void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
@@ -861,7 +862,7 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
   if (o.precond) FV_TRY(pre.alloc(n));
   const double sigma = g->sigma_default;
   const double ktol = mixed ? std::max(o.krylov_tol, 1e-5) : o.krylov_tol;
-  double r0 = -1.0;
+  double r0 = -1.0, r_prev = -1.0, eta_prev = 1e-2;
   int steps = 0;
   for (int it = 0;; ++it) {
     FV_TRY(launch_residual<double>(g, Gr, q, r64.p));
@@ -880,7 +881,8 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
       rep->residual = rn;
       rep->newton_steps = steps;
     }
-    if (rn <= o.tol * std::max(1.0, r0)) return FV_OK;
+    const double target = o.tol * std::max(1.0, r0);
+    if (rn <= target) return FV_OK;
     if (steps >= o.max_newton) return FV_ENOCONV;
     // solve (P J(q)) delta = -P F(q)
     const R* qop;
@@ -900,10 +902,22 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
     Operator<R> A{g, Gr, sigma, qop, &mv};
     A.pre = o.precond ? pre.p : nullptr;
     SolveInfo info;
-    FV_TRY(bicgstab2<R>(A, b, x.p, ktol, o.max_matvec, work.p, info));
+    // inner tolerance: fixed krylov_tol, or Eisenstat-Walker (choice 2): eta = 0.9 (r_k / r_{k-1})^2,
+    // at most 1e-2 (safeguard max(eta, 0.9 eta_{k-1}^2)), at least krylov_tol and half of what takes the
+    // residual to the Newton target in this step (no over-solving near the round-off floor)
+    double eta = ktol;
+    if (o.forcing) {
+      eta = (r_prev > 0.0) ? 0.9 * (rn / r_prev) * (rn / r_prev) : 1e-2;
+      eta = std::max(eta, 0.9 * eta_prev * eta_prev);
+      eta = std::min(eta, 1e-2);
+      eta = std::max(eta, std::max(ktol, 0.5 * target / rn));
+    }
+    eta_prev = eta;
+    r_prev = rn;
+    FV_TRY(bicgstab2<R>(A, b, x.p, eta, o.max_matvec, work.p, info));
     if (info.status != FV_OK && (info.breakdown || info.stalled)) {
       SolveInfo info2;
-      FV_TRY(gmres<R>(A, b, x.p, ktol, o.gmres_m, o.max_matvec - info.matvecs, basis.p, w.p, info2));
+      FV_TRY(gmres<R>(A, b, x.p, eta, o.gmres_m, o.max_matvec - info.matvecs, basis.p, w.p, info2));
       rep->gmres_fallbacks += 1;
     }
     rep->matvecs += (int)mv;
@@ -935,7 +949,8 @@ extern "C" int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_new
   else
     fv_newton_default_opts(&o);
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
-  if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200 || o.precond < 0 || o.precond > 1)
+  if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200 || o.precond < 0 || o.precond > 1 ||
+      o.forcing < 0 || o.forcing > 1)
     return invalid("bad Newton options");
   fv_newton_report rep;
   std::memset(&rep, 0, sizeof(rep));
