@@ -154,7 +154,8 @@ int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst);
 typedef struct {
     int precision;        /* FV_FP64: everything FP64.  FV_FP32: Krylov vectors and
                              J.v+projection in FP32; residual, updates and inner
-                             products FP64 (the outer loop refines to FP64). */
+                             products FP64 (the outer loop refines to FP64); inner
+                             tolerances are kept >= 1e-3 (preconditioned) or 1e-5 */
     double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) */
     double krylov_tol;    /* relative residual of each inner solve (forcing = 0), or its floor */
     int max_newton;       /* Newton steps */
@@ -176,9 +177,9 @@ typedef struct {
     int matvecs;          /* J.v+projections, all continuation steps */
     int gmres_fallbacks;  /* inner solves finished by GMRES */
     int continuation_steps;
-    double residual0;     /* ||P F(q)||_inf at the start of the final Gr */
+    double residual0;     /* ||P F(q)||_inf at the start of the final Gr (or of the Gr that failed) */
     double residual;      /* ||P F(q)||_inf at the end (FP64) */
-    double history[64];   /* ||P F||_inf per Newton step at the final Gr */
+    double history[64];   /* ||P F||_inf per Newton step at the final (or failed) Gr */
 } fv_newton_report;
 
 void fv_newton_default_opts(fv_newton_opts* o);

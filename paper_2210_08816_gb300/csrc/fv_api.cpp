@@ -861,7 +861,10 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
   DevBuf<R> pre;
   if (o.precond) FV_TRY(pre.alloc(n));
   const double sigma = g->sigma_default;
-  const double ktol = mixed ? std::max(o.krylov_tol, 1e-5) : o.krylov_tol;
+  // FP32 inner solves stall near u_32 times the stiffness ratio of what they apply: ~1e-5 unpreconditioned,
+  // ~1e-3 through M^-1 = P L^-1 (L^-1 x is smooth, so J L^-1 x carries u_32 lam_max / lam_min of round-off);
+  // the FP64 outer loop refines past either
+  const double ktol = mixed ? std::max(o.krylov_tol, o.precond ? 1e-3 : 1e-5) : o.krylov_tol;
   double r0 = -1.0, r_prev = -1.0, eta_prev = 1e-2;
   int steps = 0;
   for (int it = 0;; ++it) {
@@ -971,6 +974,13 @@ extern "C" int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_new
     if (!last) {
       rep.matvecs += tmp.matvecs;
       rep.gmres_fallbacks += tmp.gmres_fallbacks;
+      if (st != FV_OK) {  // report the Gr point that failed: its residual history and Newton steps
+        rep.newton_steps = tmp.newton_steps;
+        rep.residual0 = tmp.residual0;
+        rep.residual = tmp.residual;
+        std::memcpy(rep.history, tmp.history, sizeof(rep.history));
+        break;
+      }
       rep.continuation_steps += 1;
     }
     if (st != FV_OK) break;
