@@ -187,7 +187,11 @@ void fv_newton_default_opts(fv_newton_opts* o);
 /* Steady state by Newton's method (Section 1 methods paragraph): solve
  * P F(q) = 0 for divergence-free q; corrections from (P J(q)) delta = -P F(q)
  * by BiCGstab(2) (Sleijpen & Fokkema), with GMRES(m) taking over from the
- * current iterate on breakdown or stagnation.  q_inout: device double[4N],
+ * current iterate on breakdown or stagnation.  Each correction is scaled
+ * back (1, 1/2, .., 1/16) until ||P F||_inf decreases.  Converged when
+ * ||P F||_inf <= tol max(1, r0), or at the FP64 round-off floor of ||P F||:
+ * 1e5 below r0 and not halved over three steps (report->residual says
+ * where it stopped).  q_inout: device double[4N],
  * the initial state (its velocity must be divergence free, e.g. conduction
  * u = 0, T = 1 - x) and on return the last iterate.  Returns FV_OK,
  * FV_ENOCONV (report filled, q holds the last iterate), FV_ENAN, FV_EINVAL,
