@@ -189,9 +189,9 @@ void fv_newton_default_opts(fv_newton_opts* o);
  * by BiCGstab(2) (Sleijpen & Fokkema), with GMRES(m) taking over from the
  * current iterate on breakdown or stagnation.  Each correction is scaled
  * back (1, 1/2, .., 1/16) until ||P F||_inf decreases.  Converged when
- * ||P F||_inf <= tol max(1, r0), or at the FP64 round-off floor of ||P F||:
- * 1e5 below r0 and not halved over three steps (report->residual says
- * where it stopped).  q_inout: device double[4N],
+ * ||P F||_inf <= tol max(1, r0), or when it is below its FP64 round-off
+ * floor, estimated as 1e3 eps max|q| (Gr + sum_d 4 / h_min,d^2) (above
+ * tol r0 on fine stretched grids; report->residual says where it stopped).  q_inout: device double[4N],
  * the initial state (its velocity must be divergence free, e.g. conduction
  * u = 0, T = 1 - x) and on return the last iterate.  Returns FV_OK,
  * FV_ENOCONV (report filled, q holds the last iterate), FV_ENAN, FV_EINVAL,
