@@ -159,8 +159,9 @@ typedef struct {
     double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) */
     double krylov_tol;    /* relative residual of each inner solve (forcing = 0), or its floor */
     int max_newton;       /* Newton steps */
-    int max_matvec;       /* J.v+projections per inner solve */
-    int gmres_m;          /* restart length of the GMRES fallback */
+    int max_matvec;       /* J.v+projections per inner solve (default 8000) */
+    int gmres_m;          /* restart length of the GMRES fallback (default 100; 30 stalled at
+                             64^3, Gr = 4e7) */
     double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr */
     double gr_ratio;      /* continuation factor per step (> 1) */
     int precond;          /* 1 (default): right preconditioner M^-1 = P L^-1, L the diffusion

@@ -814,8 +814,8 @@ void fv_newton_default_opts(fv_newton_opts* o) {
   o->tol = 1e-10;
   o->krylov_tol = 1e-10;
   o->max_newton = 20;
-  o->max_matvec = 4000;
-  o->gmres_m = 30;
+  o->max_matvec = 8000;
+  o->gmres_m = 100;
   o->gr_start = 0.0;
   o->gr_ratio = 2.0;
   o->precond = 1;
