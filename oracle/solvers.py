@@ -229,14 +229,30 @@ def _level(z, d, c2):
     return np.maximum(w1, w2)
 
 
+def ellipse_right_end(d, c2, level):
+    """Rightmost real point of the confocal ellipse of the given level: z = d + c (w + 1/w) / 2 with
+    |w| = level; w = level for real foci (c^2 > 0), w = -i level for imaginary foci, a circle of radius
+    `level` about d for c^2 = 0."""
+    if abs(c2) < 1e-300:
+        return d + level
+    if c2 > 0.0:
+        return d + np.sqrt(c2) * (level + 1.0 / level) / 2.0
+    return d + np.sqrt(-c2) * (level - 1.0 / level) / 2.0
+
+
 def best_ellipse(wanted, unwanted):
     """Scan a family of real-centred ellipses; return (d, c2, rate) maximising the slowest
-    wanted damping rate min_w level(w)/max_u level(u)."""
+    wanted damping rate min_w level(w)/max_u level(u), among the ellipses (through the outermost
+    unwanted value) whose rightmost real point stays left of every wanted real part: anything on the
+    real axis further right would rank among the wanted and must not be damped (at high Gr the first
+    Ritz values are far-off ones with large imaginary parts, and an ellipse around them can cover the
+    leading eigenvalues near the origin).  Without such an ellipse in the scan, the best of all."""
     ur = np.real(unwanted)
     a_min, a_max = float(np.min(ur)), float(np.max(ur))
     span = max(a_max - a_min, 1e-12 * max(1.0, abs(a_max)))
     b_max = float(np.max(np.abs(np.imag(unwanted)))) if len(unwanted) else 0.0
-    best = None
+    w_left = float(np.min(np.real(wanted)))
+    best, best_ok = None, None
     for fd in np.linspace(0.2, 0.8, 13):
         d = a_min + fd * span
         a0 = max(a_max - d, d - a_min)
@@ -247,7 +263,9 @@ def best_ellipse(wanted, unwanted):
             rate = lw / lu if lu > 0 else np.inf
             if best is None or rate > best[2]:
                 best = (d, c2, rate)
-    return best
+            if ellipse_right_end(d, c2, lu) <= w_left and (best_ok is None or rate > best_ok[2]):
+                best_ok = (d, c2, rate)
+    return best_ok if best_ok is not None else best
 
 
 def chebyshev_filter(A, y0, d, c2, lam_ref, degree):
