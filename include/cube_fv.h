@@ -89,7 +89,10 @@ int fv_residual(fv_grid g, double Gr, const double* q, double* F);
 
 /* Jacobian-vector product J(q) v, the exact derivative of F (F is quadratic):
  * J v = -div(q v) - div(v q) + Lap v + Gr T_v e_z, thermal Dirichlet data 0.
- * prec selects the element type of q, v and Jv.  Errors: FV_EINVAL, FV_ECUDA. */
+ * prec selects the element type of q, v and Jv.  The wall slot (slot 0 along
+ * its own axis) of u, v and w must hold zero in q and in v, as every state
+ * and vector this library writes does: the kernel reads it as the wall value.
+ * Errors: FV_EINVAL, FV_ECUDA. */
 int fv_jvp(fv_grid g, int prec, double Gr, const void* q, const void* v, void* Jv);
 
 /* SIMPLE-like projection (Section 1 methods paragraph, Section 3): replaces the

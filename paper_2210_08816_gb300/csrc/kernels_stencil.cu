@@ -249,17 +249,21 @@ __device__ __forceinline__ const AxM<R>& axm(const AxM<R>& x, const AxM<R>& y, c
 
 // Same mathematics as momentum_terms / temperature_terms, reading neighbours from the ring.
 // Arrays 0..3 are the advecting state a, arrays AB..AB+3 the advected field b (AB = 0 for F, 4 for J.v).
-template <typename R, int C, int NA, int AB>
+// GHOST (J.v, homogeneous wall data): the wall cases need no branches, because the general formulas give
+// them when they read zeros there: the face-normal wall slot 0 holds zero, everything outside the domain
+// arrives zero-filled in the ring, and the metric arrays hold the wall values (idc[0] = 2 / dx_0,
+// idc[n] = 2 / dx_{n-1}, wl = wr = 0 on the wall faces).  Only T's zero-flux walls (y, z) keep theirs.
+template <typename R, int C, int NA, int AB, bool GHOST>
 __device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3], const AxM<R>& mx,
                                               const AxM<R>& my, const AxM<R>& mz, R& conv, R& lap) {
   constexpr int cx = unit(C, 0), cy = unit(C, 1), cz = unit(C, 2);
   const AxM<R>& MC = axm<C>(mx, my, mz);
   const int pc = p[C], nc = g.n[C];
   const R aH = S.at(C, 0, 0, 0), bH = S.at(AB + C, 0, 0, 0);
-  const R aM = (pc >= 2) ? S.at(C, -cx, -cy, -cz) : R(0);
-  const R bM = (pc >= 2) ? S.at(AB + C, -cx, -cy, -cz) : R(0);
-  const R aP = (pc + 1 < nc) ? S.at(C, cx, cy, cz) : R(0);
-  const R bP = (pc + 1 < nc) ? S.at(AB + C, cx, cy, cz) : R(0);
+  const R aM = (GHOST || pc >= 2) ? S.at(C, -cx, -cy, -cz) : R(0);
+  const R bM = (GHOST || pc >= 2) ? S.at(AB + C, -cx, -cy, -cz) : R(0);
+  const R aP = (GHOST || pc + 1 < nc) ? S.at(C, cx, cy, cz) : R(0);
+  const R bP = (GHOST || pc + 1 < nc) ? S.at(AB + C, cx, cy, cz) : R(0);
   const R aE = R(0.5) * (aH + aP), bE = R(0.5) * (bH + bP);
   const R aW = R(0.5) * (aM + aH), bW = R(0.5) * (bM + bH);
   conv = R(2) * (aE * bE - aW * bW) * MC.ic;
@@ -272,7 +276,7 @@ __device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>
     const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
     const int pd = p[D], nd = g.n[D];
     R fLo = R(0), fHi = R(0), gLo, gHi;
-    if (pd >= 1) {
+    if (GHOST || pd >= 1) {
       const R aDc = wlC * S.at(D, -cx, -cy, -cz) + wrC * S.at(D, 0, 0, 0);
       const R bDc = wlC * S.at(AB + D, -cx, -cy, -cz) + wrC * S.at(AB + D, 0, 0, 0);
       const R bCm = S.at(AB + C, -dx, -dy, -dz), aCm = S.at(C, -dx, -dy, -dz);
@@ -283,7 +287,7 @@ __device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>
     } else {
       gLo = bH * MD.ic0;
     }
-    if (pd + 1 <= nd - 1) {
+    if (GHOST || pd + 1 <= nd - 1) {
       const R aDc = wlC * S.at(D, dx - cx, dy - cy, dz - cz) + wrC * S.at(D, dx, dy, dz);
       const R bDc = wlC * S.at(AB + D, dx - cx, dy - cy, dz - cz) + wrC * S.at(AB + D, dx, dy, dz);
       const R bCp = S.at(AB + C, dx, dy, dz), aCp = S.at(C, dx, dy, dz);
@@ -299,7 +303,7 @@ __device__ __forceinline__ void momentum_ring(const Geo<R>& g, const Ring<R, NA>
   }
 }
 
-template <typename R, int NA, int AB>
+template <typename R, int NA, int AB, bool GHOST>
 __device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, NA>& S, const int p[3],
                                                  const AxM<R>& mx, const AxM<R>& my, const AxM<R>& mz, R T_hot,
                                                  R& conv, R& lap) {
@@ -312,14 +316,14 @@ __device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, 
     const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
     const int pd = p[D], nd = g.n[D];
     R fLo = R(0), fHi = R(0), gLo = R(0), gHi = R(0);
-    if (pd >= 1) {
+    if ((GHOST && D == 0) || pd >= 1) {  // x: Dirichlet T = 0 of J (ghost zero); y, z: zero flux
       const R Tam = S.at(3, -dx, -dy, -dz), Tbm = S.at(AB + 3, -dx, -dy, -dz);
       fLo = S.at(D, 0, 0, 0) * (MD.wl * Tbm + MD.wr * TbH) + S.at(AB + D, 0, 0, 0) * (MD.wl * Tam + MD.wr * TaH);
       gLo = (TbH - Tbm) * MD.ic;
     } else if (D == 0) {
       gLo = (TbH - T_hot) * MD.ic0;
     }
-    if (pd + 1 <= nd - 1) {
+    if ((GHOST && D == 0) || pd + 1 <= nd - 1) {
       const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
       fHi = S.at(D, dx, dy, dz) * (MD.wlp * TbH + MD.wrp * Tbp) +
             S.at(AB + D, dx, dy, dz) * (MD.wlp * TaH + MD.wrp * Tap);
@@ -471,7 +475,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
       const int o = (k * ny + j) * nx + i;
       R conv, lap;
       if (i >= 1) {
-        momentum_ring<R, 0, NA, AB>(g, S, p, mx, my, mz, conv, lap);
+        momentum_ring<R, 0, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
         R r = lap - half * conv;
         if (MODE == 1) r -= sigma * S.at(AB + 0, 0, 0, 0);
         out[o] = r;
@@ -479,7 +483,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
         out[o] = R(0);
       }
       if (j >= 1) {
-        momentum_ring<R, 1, NA, AB>(g, S, p, mx, my, mz, conv, lap);
+        momentum_ring<R, 1, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
         R r = lap - half * conv;
         if (MODE == 1) r -= sigma * S.at(AB + 1, 0, 0, 0);
         out[N + o] = r;
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
         out[N + o] = R(0);
       }
       if (k >= 1) {
-        momentum_ring<R, 2, NA, AB>(g, S, p, mx, my, mz, conv, lap);
+        momentum_ring<R, 2, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
         const R Tf = mz.wl * S.at(AB + 3, 0, 0, -1) + mz.wr * S.at(AB + 3, 0, 0, 0);
         R r = lap - half * conv + Gr * Tf;
         if (MODE == 1) r -= sigma * S.at(AB + 2, 0, 0, 0);
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
       } else {
         out[2 * N + o] = R(0);
       }
-      temperature_ring<R, NA, AB>(g, S, p, mx, my, mz, (MODE == 0) ? R(1) : R(0), conv, lap);
+      temperature_ring<R, NA, AB, MODE == 1>(g, S, p, mx, my, mz, (MODE == 0) ? R(1) : R(0), conv, lap);
       R r = lap * invPr - half * conv;
       if (MODE == 1) r -= sigma * S.at(AB + 3, 0, 0, 0);
       out[3 * N + o] = r;
