@@ -68,6 +68,7 @@ struct TcState {
   // per axis: [fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi, bwd_s_lo, bwd_a_hi, bwd_a_lo]
   CUtensorMap B[3][8];
   const float* lam[3] = {nullptr, nullptr, nullptr};  // eigenvalues in the tensor-core mode order
+  int sms = 0;  // multiprocessors of the device (grid of the persistent passes)
 };
 }  // namespace fv
 

@@ -344,6 +344,241 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// Persistent form of the same pass: one CTA per SM walks the tiles blockIdx.x, +gridDim.x, ...; the
+// shared-memory ring's phases run on across tiles (global stage counter), and two TMEM accumulators
+// (columns 0 and 256) let a separate epilogue warpgroup drain tile t while the MMAs of tile t + 1 run.
+// Warps: 0 TMA producer, 1 MMA issuer, 2-5 converters (row t of the A tiles), 6-9 epilogue.
+constexpr int kTcpThreads = 320;
+constexpr bool kTcPersistent = true;  // the one-tile-per-CTA kernel above stays as the reference form
+
+template <bool SCALE, bool BWD>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+    k_transform_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB1hi,
+                    const __grid_constant__ CUtensorMap tmB1lo, const __grid_constant__ CUtensorMap tmB2hi,
+                    const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int n,
+                    const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
+                    int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_conv[kTcStages], bar_empty[kTcStages];
+  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ float lz_s[256];
+  const int h = n / 2;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t b_bytes = (uint32_t)h * kTcRowBytes;
+  const uint32_t stage_bytes = 4u * kTcABytes + 4u * b_bytes;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nst = n / (2 * kTcBK);
+  const int ntiles = (P + kTcBM - 1) / kTcBM;
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_conv[s]), 128);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_accf[b]), 1);
+      mbar_init(smem_u32(&bar_acce[b]), 4);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (SCALE)
+    for (int m = threadIdx.x; m < n; m += kTcpThreads) lz_s[m] = lz[m];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int ti = 0; ti < my_tiles && ok; ++ti) {
+        const int p0 = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM;
+        for (int j = 0; j < nst; ++j) {
+          const int gi = ti * nst + j, st = gi % kTcStages;
+          if (gi >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((gi / kTcStages) - 1) & 1, err, 11)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sb = base + st * stage_bytes;
+          const uint32_t fb = smem_u32(&bar_full[st]);
+          const int k1 = j * kTcBK;
+          const int k2 = BWD ? h + j * kTcBK : n - kTcBK - j * kTcBK;
+          mbar_expect_tx(fb, 2u * kTcABytes + 4u * b_bytes);
+          tma_load_2d(sb, &tmA, fb, k1, p0);
+          tma_load_2d(sb + kTcABytes, &tmA, fb, k2, p0);
+          tma_load_2d(sb + 4u * kTcABytes, &tmB1hi, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 4u * kTcABytes + b_bytes, &tmB1lo, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 4u * kTcABytes + 2u * b_bytes, &tmB2hi, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 4u * kTcABytes + 3u * b_bytes, &tmB2lo, fb, j * kTcBK, 0);
+          ++issued;
+        }
+      }
+      // drain: every issued copy has landed before the block may exit
+      for (int gi = (issued > kTcStages ? issued - kTcStages : 0); gi < issued; ++gi)
+        mbar_wait(smem_u32(&bar_full[gi % kTcStages]), (gi / kTcStages) & 1, err, 12);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(h >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
+      bool ok = true;
+      int last = -1;  // last tile whose accumulator commit was issued
+      for (int ti = 0; ti < my_tiles && ok; ++ti) {
+        const int b = ti & 1;
+        if (ti >= 2 && !mbar_wait(smem_u32(&bar_acce[b]), ((ti / 2) - 1) & 1, err, 13)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(b * 256);
+        for (int j = 0; j < nst; ++j) {
+          const int gi = ti * nst + j, st = gi % kTcStages;
+          if (!mbar_wait(smem_u32(&bar_conv[st]), (gi / kTcStages) & 1, err, 14)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sb = base + st * stage_bytes;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const uint32_t a_hi = sb + half * kTcABytes, a_lo = sb + (2 + half) * kTcABytes;
+            const uint32_t b_hi = sb + 4u * kTcABytes + (2 * half) * b_bytes, b_lo = b_hi + b_bytes;
+            const uint32_t d = dacc + (uint32_t)(half * h);
+#pragma unroll
+            for (int kk = 0; kk < kTcBK / 8; ++kk) {
+              const uint64_t ahi = smem_desc(a_hi + kk * 32), alo = smem_desc(a_lo + kk * 32);
+              const uint64_t bhi = smem_desc(b_hi + kk * 32), blo = smem_desc(b_lo + kk * 32);
+              mma_tf32(d, ahi, bhi, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+              mma_tf32(d, ahi, blo, idesc, 1u);
+              mma_tf32(d, alo, bhi, idesc, 1u);
+            }
+          }
+          mma_commit(smem_u32(&bar_empty[st]));
+        }
+        mma_commit(smem_u32(&bar_accf[b]));  // arrives once every MMA issued so far has completed
+        last = ti;
+      }
+      // on an early exit, wait (bounded) for the MMAs already issued before the accumulators are freed
+      if (!ok && last >= 0) mbar_wait(smem_u32(&bar_accf[last & 1]), (last / 2) & 1, err, 16);
+    }
+  } else if (warp < 6) {
+    // converters: thread t owns row t of every stage's A tiles
+    const int t = threadIdx.x - 64;
+    const int x = (t >> 1) & 3;  // swizzle pattern of this row
+    bool ok = true;
+    for (int ti = 0; ti < my_tiles && ok; ++ti) {
+      for (int j = 0; j < nst; ++j) {
+        const int gi = ti * nst + j, st = gi % kTcStages;
+        if (!mbar_wait(smem_u32(&bar_full[st]), (gi / kTcStages) & 1, err, 17)) {
+          ok = false;
+          break;
+        }
+        unsigned char* sp = smem_raw + ((base + st * stage_bytes) - smem_u32(smem_raw)) + t * kTcRowBytes;
+        float4* a1 = reinterpret_cast<float4*>(sp);
+        float4* a2 = reinterpret_cast<float4*>(sp + kTcABytes);
+        float4* l1 = reinterpret_cast<float4*>(sp + 2 * kTcABytes);
+        float4* l2 = reinterpret_cast<float4*>(sp + 3 * kTcABytes);
+        if (BWD) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float4 hh, ll;
+            split4(a1[c], hh, ll);
+            a1[c] = hh;
+            l1[c] = ll;
+            split4(a2[c], hh, ll);
+            a2[c] = hh;
+            l2[c] = ll;
+          }
+        } else {
+          float4 av[4], mv[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            av[c] = a1[c ^ x];
+            mv[c] = a2[(3 - c) ^ x];
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float4 a = av[c], m = mv[c];
+            const float4 sum = make_float4(a.x + m.w, a.y + m.z, a.z + m.y, a.w + m.x);
+            const float4 dif = make_float4(a.x - m.w, a.y - m.z, a.z - m.y, a.w - m.x);
+            float4 hh, ll;
+            split4(sum, hh, ll);
+            a1[c ^ x] = hh;
+            l1[c ^ x] = ll;
+            split4(dif, hh, ll);
+            a2[c ^ x] = hh;
+            l2[c ^ x] = ll;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&bar_conv[st]));
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, one row of the tile per thread
+    const int q = warp % 4;
+    const int row = q * 32 + lane;
+    for (int ti = 0; ti < my_tiles; ++ti) {
+      const int b = ti & 1;
+      const bool ok = mbar_wait(smem_u32(&bar_accf[b]), (ti / 2) & 1, err, 18);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int p = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM + row;
+      float sa = 0.f, sb2 = 0.f;
+      int pa = 0, pb = 0;
+      if (SCALE && p < P) {
+        pa = p / nb;
+        pb = p - pa * nb;
+        sa = ly[pa];
+        sb2 = lx[pb];
+      }
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
+      for (int c0 = 0; c0 < h; c0 += 16) {
+        uint32_t r1[16], r2[16];
+        tmem_ld16(lane_base + (uint32_t)c0, r1);
+        tmem_ld16(lane_base + (uint32_t)(h + c0), r2);
+        if (p < P) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int m = c0 + jj;
+            const float v1 = __uint_as_float(r1[jj]), v2 = __uint_as_float(r2[jj]);
+            if (BWD) {  // cells m and n-1-m
+              out[(long long)m * P + p] = v1 + v2;
+              out[(long long)(n - 1 - m) * P + p] = v1 - v2;
+            } else if (SCALE) {  // symmetric mode m, antisymmetric mode h + m
+              const float s1 = (m == 0 && pa == 0 && pb == 0) ? 0.f : v1 * rcp_approx(lz_s[m] + sa + sb2);
+              out[(long long)m * P + p] = s1;
+              out[(long long)(h + m) * P + p] = v2 * rcp_approx(lz_s[h + m] + sa + sb2);
+            } else {
+              out[(long long)m * P + p] = v1;
+              out[(long long)(h + m) * P + p] = v2;
+            }
+          }
+        }
+      }
+      // the accumulator's values are in registers (tcgen05.wait::ld): the MMAs may reuse it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce[b]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -516,6 +751,15 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<dou
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  {
+    int dev = 0, sms = 0;
+    FV_CUDA(cudaGetDevice(&dev));
+    FV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    g->tc.sms = sms;
+  }
   g->tc.ready = true;
   return FV_OK;
 }
@@ -527,10 +771,25 @@ int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float*
   const long long P = (long long)na * nb;
   CUtensorMap tmA;
   FV_TRY(encode(&tmA, in, P, n, kTcBM));
-  const dim3 grid((unsigned)((P + kTcBM - 1) / kTcBM));
+  const long long ntiles = (P + kTcBM - 1) / kTcBM;
+  const dim3 grid((unsigned)ntiles);
   const size_t smem = tc_smem_bytes(n);
   const CUtensorMap* B = g->tc.B[axis] + (bwd ? 4 : 0);
   ProfScope ps(g, PROF_TRANSFORM_TC);
+  if (kTcPersistent && g->tc.sms > 0) {
+    const dim3 pgrid((unsigned)std::min<long long>(ntiles, g->tc.sms));
+    if (bwd)
+      k_transform_tcp<false, true><<<pgrid, kTcpThreads, smem, g->stream>>>(tmA, B[0], B[1], B[2], B[3], out, (int)P,
+                                                                          n, nullptr, nullptr, nullptr, nb, g->ws.err);
+    else if (scale)
+      k_transform_tcp<true, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb, g->ws.err);
+    else
+      k_transform_tcp<false, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, n, nullptr, nullptr, nullptr, nb, g->ws.err);
+    FV_CUDA(cudaGetLastError());
+    return FV_OK;
+  }
   if (bwd)
     k_transform_tc<false, true><<<grid, kTcThreads, smem, g->stream>>>(tmA, B[0], B[1], B[2], B[3], out, (int)P, n,
                                                                        nullptr, nullptr, nullptr, nb, g->ws.err);
