@@ -316,20 +316,30 @@ __device__ __forceinline__ void temperature_ring(const Geo<R>& g, const Ring<R, 
     const int dx = unit(D, 0), dy = unit(D, 1), dz = unit(D, 2);
     const int pd = p[D], nd = g.n[D];
     R fLo = R(0), fHi = R(0), gLo = R(0), gHi = R(0);
-    if ((GHOST && D == 0) || pd >= 1) {  // x: Dirichlet T = 0 of J (ghost zero); y, z: zero flux
+    if constexpr (GHOST) {  // one basic block: x Dirichlet T = 0 by the ghost zero, y / z zero flux by a select
+      const R Tam = S.at(3, -dx, -dy, -dz), Tbm = S.at(AB + 3, -dx, -dy, -dz);
+      fLo = S.at(D, 0, 0, 0) * (MD.wl * Tbm + MD.wr * TbH) + S.at(AB + D, 0, 0, 0) * (MD.wl * Tam + MD.wr * TaH);
+      gLo = (D == 0 || pd >= 1) ? (TbH - Tbm) * MD.ic : R(0);
+      const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
+      fHi = S.at(D, dx, dy, dz) * (MD.wlp * TbH + MD.wrp * Tbp) +
+            S.at(AB + D, dx, dy, dz) * (MD.wlp * TaH + MD.wrp * Tap);
+      gHi = (D == 0 || pd + 1 <= nd - 1) ? (Tbp - TbH) * MD.icp : R(0);
+    } else if (pd >= 1) {
       const R Tam = S.at(3, -dx, -dy, -dz), Tbm = S.at(AB + 3, -dx, -dy, -dz);
       fLo = S.at(D, 0, 0, 0) * (MD.wl * Tbm + MD.wr * TbH) + S.at(AB + D, 0, 0, 0) * (MD.wl * Tam + MD.wr * TaH);
       gLo = (TbH - Tbm) * MD.ic;
     } else if (D == 0) {
       gLo = (TbH - T_hot) * MD.ic0;
     }
-    if ((GHOST && D == 0) || pd + 1 <= nd - 1) {
-      const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
-      fHi = S.at(D, dx, dy, dz) * (MD.wlp * TbH + MD.wrp * Tbp) +
-            S.at(AB + D, dx, dy, dz) * (MD.wlp * TaH + MD.wrp * Tap);
-      gHi = (Tbp - TbH) * MD.icp;
-    } else if (D == 0) {
-      gHi = -TbH * MD.icn;
+    if constexpr (!GHOST) {
+      if (pd + 1 <= nd - 1) {
+        const R Tap = S.at(3, dx, dy, dz), Tbp = S.at(AB + 3, dx, dy, dz);
+        fHi = S.at(D, dx, dy, dz) * (MD.wlp * TbH + MD.wrp * Tbp) +
+              S.at(AB + D, dx, dy, dz) * (MD.wlp * TaH + MD.wrp * Tap);
+        gHi = (Tbp - TbH) * MD.icp;
+      } else if (D == 0) {
+        gHi = -TbH * MD.icn;
+      }
     }
     conv += (fHi - fLo) * MD.ix;
     lap += (gHi - gLo) * MD.ix;
@@ -378,7 +388,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* err
 // MODE 0: residual (arrays: q), MODE 1: J.v (arrays: q then v).  use_tma: plane tiles arrive by one 4D TMA
 // box per state (x, y, z, field) with zero fill outside the domain; otherwise by per-element cp.async.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kTX * kTY, 3)
+__global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
     k_stencil_z(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int use_tma,
                 int* err, Geo<R> g, int N, R Gr, R invPr, R sigma, const R* __restrict__ q, const R* __restrict__ v,
                 R* __restrict__ out) {
@@ -474,35 +484,53 @@ __global__ void __launch_bounds__(kTX * kTY, 3)
       const int p[3] = {i, j, k};
       const int o = (k * ny + j) * nx + i;
       R conv, lap;
-      if (i >= 1) {
-        momentum_ring<R, 0, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
-        R r = lap - half * conv;
-        if (MODE == 1) r -= sigma * S.at(AB + 0, 0, 0, 0);
-        out[o] = r;
-      } else {
-        out[o] = R(0);
-      }
-      if (j >= 1) {
-        momentum_ring<R, 1, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
-        R r = lap - half * conv;
-        if (MODE == 1) r -= sigma * S.at(AB + 1, 0, 0, 0);
-        out[N + o] = r;
-      } else {
-        out[N + o] = R(0);
-      }
-      if (k >= 1) {
-        momentum_ring<R, 2, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
+      if constexpr (MODE == 1) {
+        // J.v: all four equations in one basic block (the wall outputs by selects), so that the compiler
+        // can share the ring loads between them
+        momentum_ring<R, 0, NA, AB, true>(g, S, p, mx, my, mz, conv, lap);
+        const R r0 = lap - conv - sigma * S.at(AB + 0, 0, 0, 0);
+        momentum_ring<R, 1, NA, AB, true>(g, S, p, mx, my, mz, conv, lap);
+        const R r1 = lap - conv - sigma * S.at(AB + 1, 0, 0, 0);
+        momentum_ring<R, 2, NA, AB, true>(g, S, p, mx, my, mz, conv, lap);
         const R Tf = mz.wl * S.at(AB + 3, 0, 0, -1) + mz.wr * S.at(AB + 3, 0, 0, 0);
-        R r = lap - half * conv + Gr * Tf;
-        if (MODE == 1) r -= sigma * S.at(AB + 2, 0, 0, 0);
-        out[2 * N + o] = r;
+        const R r2 = lap - conv + Gr * Tf - sigma * S.at(AB + 2, 0, 0, 0);
+        temperature_ring<R, NA, AB, true>(g, S, p, mx, my, mz, R(0), conv, lap);
+        const R r3 = lap * invPr - conv - sigma * S.at(AB + 3, 0, 0, 0);
+        out[o] = (i >= 1) ? r0 : R(0);
+        out[N + o] = (j >= 1) ? r1 : R(0);
+        out[2 * N + o] = (k >= 1) ? r2 : R(0);
+        out[3 * N + o] = r3;
       } else {
-        out[2 * N + o] = R(0);
+        if (i >= 1) {
+          momentum_ring<R, 0, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
+          R r = lap - half * conv;
+          if (MODE == 1) r -= sigma * S.at(AB + 0, 0, 0, 0);
+          out[o] = r;
+        } else {
+          out[o] = R(0);
+        }
+        if (j >= 1) {
+          momentum_ring<R, 1, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
+          R r = lap - half * conv;
+          if (MODE == 1) r -= sigma * S.at(AB + 1, 0, 0, 0);
+          out[N + o] = r;
+        } else {
+          out[N + o] = R(0);
+        }
+        if (k >= 1) {
+          momentum_ring<R, 2, NA, AB, MODE == 1>(g, S, p, mx, my, mz, conv, lap);
+          const R Tf = mz.wl * S.at(AB + 3, 0, 0, -1) + mz.wr * S.at(AB + 3, 0, 0, 0);
+          R r = lap - half * conv + Gr * Tf;
+          if (MODE == 1) r -= sigma * S.at(AB + 2, 0, 0, 0);
+          out[2 * N + o] = r;
+        } else {
+          out[2 * N + o] = R(0);
+        }
+        temperature_ring<R, NA, AB, MODE == 1>(g, S, p, mx, my, mz, (MODE == 0) ? R(1) : R(0), conv, lap);
+        R r = lap * invPr - half * conv;
+        if (MODE == 1) r -= sigma * S.at(AB + 3, 0, 0, 0);
+        out[3 * N + o] = r;
       }
-      temperature_ring<R, NA, AB, MODE == 1>(g, S, p, mx, my, mz, (MODE == 0) ? R(1) : R(0), conv, lap);
-      R r = lap * invPr - half * conv;
-      if (MODE == 1) r -= sigma * S.at(AB + 3, 0, 0, 0);
-      out[3 * N + o] = r;
     }
     if (!use_tma) cp_async_wait_all();  // plane k+2 has landed
     __syncthreads();                    // nobody reads the slot of plane k-1 any more
