@@ -178,7 +178,9 @@ def g_faces(n):
 # ----------------------------------------------------------------------------- GPU arm
 def run_steps(fv, g, prec, q, ya, yb, K, stream, sigma, profile=False):
     """K recurrence steps y_{j+1} = 2 t (A - d) y_j - c2 t t' y_{j-1} (fixed coefficients of a
-    degree-K Chebyshev filter on [-2|sigma|, 0]) + FP64 norm read-back; returns (ms, last norm)."""
+    degree-K Chebyshev filter on [-2|sigma|, 0]), each with its FP64 norm summed in the correction pass
+    and stored on the device (stream-ordered); the norms are read back every 16 steps for the overflow
+    guard, as the library's own filter does; returns (ms, last norm)."""
     import torch
     d, c2 = sigma, sigma * sigma * 0.9
     s = 10.0 - d
@@ -187,13 +189,16 @@ def run_steps(fv, g, prec, q, ya, yb, K, stream, sigma, profile=False):
     stop = torch.cuda.Event(enable_timing=True)
     if profile:
         fv.fv_profile(g, True)
+    norms = torch.zeros(K, dtype=torch.float64, device=ya.device)
     start.record(stream)
     nrm = 0.0
-    for _ in range(K):
+    for i in range(K):
         tn = 1.0 / (2.0 * s - c2 * tau)
         # yb <- 2 tn (A - d) ya - c2 tau tn yb   (A = P(J - sigma) + sigma)
-        nrm = fv.fv_jvp_project_lincomb(g, prec, GR, sigma, q, ya, yb, 2.0 * tn, -2.0 * tn * d, -c2 * tau * tn, yb,
-                                        want_norm=True)
+        fv.fv_jvp_project_lincomb_dev(g, prec, GR, sigma, q, ya, yb, 2.0 * tn, -2.0 * tn * d, -c2 * tau * tn, yb,
+                                      norm2=norms[i:i + 1])
+        if i % 16 == 15 or i == K - 1:
+            nrm = float(norms[i].item())
         if nrm > 1e30 or nrm < 1e-30:
             sc = 1.0 / nrm ** 0.5
             fv.fv_axpby(g, prec, 0.0, yb, sc, yb)

@@ -123,6 +123,15 @@ int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma,
 int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
                            const void* w, double alpha, double beta, double gamma, void* out, double* out_norm2);
 
+/* The same fused recurrence step, fully stream-ordered: ||out||^2 is summed in
+ * the same pass and written to norm2_dev (device double, may be NULL) with no
+ * host synchronisation, so that a caller running many steps reads it back only
+ * when it needs it (the filter inside arnoldi_leading checks it every 16 steps).
+ * Errors: FV_EINVAL, FV_ECUDA. */
+int fv_jvp_project_lincomb_dev(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
+                               const void* w, double alpha, double beta, double gamma, void* out,
+                               double* norm2_dev);
+
 /* Krylov inner product <a, b> over all 4N elements, accumulated in FP64 in a
  * fixed order (bit-reproducible).  result: host.  Errors: FV_EINVAL, FV_ECUDA, FV_ENAN. */
 int fv_dot(fv_grid g, int prec, const void* a, const void* b, double* result);

@@ -764,6 +764,25 @@ int fv_jvp_project(fv_grid g, int prec, double Gr, double sigma, const void* q, 
   return invalid("precision must be FV_FP64 or FV_FP32");
 }
 
+int fv_jvp_project_lincomb_dev(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
+                               const void* w, double alpha, double beta, double gamma, void* out,
+                               double* norm2_dev) {
+  if (!g || !q || !v || !out) return invalid("null argument");
+  if (out == q || out == v) return invalid("out must not alias q or v");
+  if (prec != FV_FP64 && prec != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
+  const double b2 = alpha * sigma + beta;
+  const int slot = norm2_dev ? 0 : -1;
+  if (prec == FV_FP64)
+    FV_TRY(chebyshev_step<double>(g, Gr, sigma, (const double*)q, (const double*)v, w ? (const double*)w : nullptr,
+                                  alpha, b2, w ? gamma : 0.0, (double*)out, slot));
+  else
+    FV_TRY(chebyshev_step<float>(g, Gr, sigma, (const float*)q, (const float*)v, w ? (const float*)w : nullptr, alpha,
+                                 b2, w ? gamma : 0.0, (float*)out, slot));
+  if (norm2_dev)
+    FV_CUDA(cudaMemcpyAsync(norm2_dev, g->ws.scalars, sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  return FV_OK;
+}
+
 int fv_jvp_project_lincomb(fv_grid g, int prec, double Gr, double sigma, const void* q, const void* v,
                            const void* w, double alpha, double beta, double gamma, void* out, double* out_norm2) {
   if (!g || !q || !v || !out) return invalid("null argument");

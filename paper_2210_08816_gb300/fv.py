@@ -77,6 +77,7 @@ def lib():
             "fv_project": (i, [vp, i, vp, i, d, C.POINTER(i), C.POINTER(d)]),
             "fv_jvp_project": (i, [vp, i, d, d, vp, vp, vp]),
             "fv_jvp_project_lincomb": (i, [vp, i, d, d, vp, vp, vp, d, d, d, vp, C.POINTER(d)]),
+            "fv_jvp_project_lincomb_dev": (i, [vp, i, d, d, vp, vp, vp, d, d, d, vp, vp]),
             "fv_dot": (i, [vp, i, vp, vp, C.POINTER(d)]),
             "fv_dot_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp]),
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
@@ -101,7 +102,7 @@ def lib():
 
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
-            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve",
+            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve",
             "fv_newton_default_opts",
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
@@ -211,6 +212,18 @@ def fv_jvp_project(g: Grid, prec, Gr, sigma, q, v, out):
     dt = g.dtype(prec)
     _check(lib().fv_jvp_project(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"), _ptr(v, dt, g.n, "v"),
                                 _ptr(out, dt, g.n, "out")), "fv_jvp_project")
+    return out
+
+
+def fv_jvp_project_lincomb_dev(g: Grid, prec, Gr, sigma, q, v, w, alpha, beta, gamma, out, norm2=None):
+    """The same step, stream-ordered: ||out||^2 into the device float64 tensor norm2 (one element) if given."""
+    import torch
+    dt = g.dtype(prec)
+    wp = _ptr(w, dt, g.n, "w") if w is not None else None
+    np_ = _ptr(norm2, torch.float64, 1, "norm2") if norm2 is not None else None
+    _check(lib().fv_jvp_project_lincomb_dev(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"),
+                                            _ptr(v, dt, g.n, "v"), wp, float(alpha), float(beta), float(gamma),
+                                            _ptr(out, dt, g.n, "out"), np_), "fv_jvp_project_lincomb_dev")
     return out
 
 

@@ -236,3 +236,22 @@ def test_diffusion_solve_inverts_the_oracle_diffusion(fv, shape, stretch):
     assert rel(host(out32, og.shape), got) <= TOL32_PROJ
     fv.fv_diffusion_solve(g, fv.FV_FP64, x64, x64)  # in place
     assert rel(host(x64, og.shape), got) <= 1e-14
+
+
+def test_stream_ordered_step_matches_the_synchronous_one(fv):
+    """fv_jvp_project_lincomb_dev (norm left on the device) computes the same step and the same norm as
+    fv_jvp_project_lincomb (norm read back to the host)."""
+    shape = (64, 48, 40)
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = dev(state(og, 7), torch.float32)
+    v = dev(vector(og, 8), torch.float32)
+    w = dev(vector(og, 9), torch.float32)
+    a = torch.empty_like(v)
+    nrm = fv.fv_jvp_project_lincomb(g, fv.FV_FP32, 2e5, -50.0, q, v, w, 0.3, -1.2, 0.7, a, want_norm=True)
+    b = torch.empty_like(v)
+    n2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fv.fv_jvp_project_lincomb_dev(g, fv.FV_FP32, 2e5, -50.0, q, v, w, 0.3, -1.2, 0.7, b, norm2=n2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert float(n2.item()) == nrm
