@@ -199,10 +199,10 @@ def run_steps(fv, g, prec, q, ya, yb, K, stream, sigma, profile=False):
                                       norm2=norms[i:i + 1])
         if i % 16 == 15 or i == K - 1:
             nrm = float(norms[i].item())
-        if nrm > 1e30 or nrm < 1e-30:
-            sc = 1.0 / nrm ** 0.5
-            fv.fv_axpby(g, prec, 0.0, yb, sc, yb)
-            fv.fv_axpby(g, prec, 0.0, ya, sc, ya)
+            if nrm > 1e30 or (0.0 < nrm < 1e-30):
+                sc = 1.0 / nrm ** 0.5
+                fv.fv_axpby(g, prec, 0.0, yb, sc, yb)
+                fv.fv_axpby(g, prec, 0.0, ya, sc, ya)
         ya, yb = yb, ya
         tau = tn
     stop.record(stream)
