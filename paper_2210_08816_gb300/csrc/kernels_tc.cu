@@ -256,16 +256,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       float4* a2 = reinterpret_cast<float4*>(sp + kTcABytes);
       float4* l1 = reinterpret_cast<float4*>(sp + 2 * kTcABytes);
       float4* l2 = reinterpret_cast<float4*>(sp + 3 * kTcABytes);
-      if (BWD) {  // plain hi / lo split of both slabs
+      if (BWD) {  // plain hi / lo split of both slabs, chunks visited in the swizzled order (no bank conflicts)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
+          const int pc = c ^ x;
           float4 hh, ll;
-          split4(a1[c], hh, ll);
-          a1[c] = hh;
-          l1[c] = ll;
-          split4(a2[c], hh, ll);
-          a2[c] = hh;
-          l2[c] = ll;
+          split4(a1[pc], hh, ll);
+          a1[pc] = hh;
+          l1[pc] = ll;
+          split4(a2[pc], hh, ll);
+          a2[pc] = hh;
+          l2[pc] = ll;
         }
       } else {  // r[k] +- r[n-1-k]: logical chunk c of slab j pairs with logical chunk 3-c of the mirror slab,
                 // element e with element 3-e
@@ -487,16 +488,17 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         float4* a2 = reinterpret_cast<float4*>(sp + kTcABytes);
         float4* l1 = reinterpret_cast<float4*>(sp + 2 * kTcABytes);
         float4* l2 = reinterpret_cast<float4*>(sp + 3 * kTcABytes);
-        if (BWD) {
+        if (BWD) {  // chunks in the swizzled order: no bank conflicts
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
+            const int pc = c ^ x;
             float4 hh, ll;
-            split4(a1[c], hh, ll);
-            a1[c] = hh;
-            l1[c] = ll;
-            split4(a2[c], hh, ll);
-            a2[c] = hh;
-            l2[c] = ll;
+            split4(a1[pc], hh, ll);
+            a1[pc] = hh;
+            l1[pc] = ll;
+            split4(a2[pc], hh, ll);
+            a2[pc] = hh;
+            l2[pc] = ll;
           }
         } else {
           float4 av[4], mv[4];
