@@ -142,6 +142,11 @@ template <typename R>
 int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, const R* v, double beta,
                    const R* w, double gamma, R* out, int norm_slot = -1);
 
+// FP32 J.v with two x-adjacent cells per thread (kernels_stencil2.cu): nx a multiple of 64, ny >= 16,
+// 16-byte aligned q and v (TMA plane ring).
+bool stencil_pair_eligible(const fv_grid_s* g, const float* q, const float* v);
+int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out);
+
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>
 int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp);

@@ -840,6 +840,9 @@ int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F) {
 
 template <typename R>
 int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out) {
+  if constexpr (sizeof(R) == 4) {  // two cells per thread (kernels_stencil2.cu) where its tiles fit
+    if (stencil_pair_eligible(g, q, v)) return launch_stencil_pair(g, Gr, sigma, q, v, out);
+  }
   return launch_stencil_z<R, 1>(g, Gr, sigma, q, v, out);
 }
 
