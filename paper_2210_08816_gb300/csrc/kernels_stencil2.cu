@@ -24,13 +24,40 @@ constexpr int kPZChunk = 32, kPRing = 4, kPNA = 8;
 constexpr long long kPWaitLimit = 1LL << 22;
 
 // ---------------------------------------------------------------- pair arithmetic
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 operator*(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2& operator+=(float2& a, float2 b) { a = a + b; return a; }
+// Blackwell's packed FP32 instructions (PTX add / sub / mul / fma .rn.f32x2): one instruction per pair,
+// the same IEEE round-to-nearest results as the two scalar operations.
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+// a * b + c, one rounding
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
 
 // Metric values of one axis as the stencil uses them (cell index c): per pair (float2, x) or per thread
 // (float, y and z).
@@ -53,6 +80,19 @@ __device__ __forceinline__ Bundle<float> load_bundle(const Geo<float>& g, int d,
   return m;
 }
 
+__device__ __forceinline__ Bundle<float2> broadcast(const Bundle<float>& a) {
+  Bundle<float2> m;
+  m.ix = bc(a.ix);
+  m.ixm = bc(a.ixm);
+  m.ic = bc(a.ic);
+  m.icp = bc(a.icp);
+  m.wl = bc(a.wl);
+  m.wr = bc(a.wr);
+  m.wlp = bc(a.wlp);
+  m.wrp = bc(a.wrp);
+  return m;
+}
+
 __device__ __forceinline__ Bundle<float2> load_bundle_pair(const Geo<float>& g, int c) {
   const Bundle<float> a = load_bundle(g, 0, c), b = load_bundle(g, 0, c + 1);
   Bundle<float2> m;
@@ -68,7 +108,7 @@ __device__ __forceinline__ Bundle<float2> load_bundle_pair(const Geo<float>& g, 
 }
 
 template <int D>
-__device__ __forceinline__ decltype(auto) pick(const Bundle<float2>& x, const Bundle<float>& y, const Bundle<float>& z) {
+__device__ __forceinline__ decltype(auto) pick(const Bundle<float2>& x, const Bundle<float2>& y, const Bundle<float2>& z) {
   if constexpr (D == 0)
     return (x);
   else if constexpr (D == 1)
@@ -102,38 +142,39 @@ __device__ __forceinline__ void transverse(const Ring2& S, const BC& MC, const B
   constexpr int dx = unit_(D, 0), dy = unit_(D, 1), dz = unit_(D, 2);
   constexpr int AB = 4;
   // low face
-  const float2 aDcL = MC.wl * S.ld<D, -cx, -cy, -cz>() + MC.wr * S.ld<D, 0, 0, 0>();
-  const float2 bDcL = MC.wl * S.ld<AB + D, -cx, -cy, -cz>() + MC.wr * S.ld<AB + D, 0, 0, 0>();
+  const float2 aDcL = fma2(MC.wl, S.ld<D, -cx, -cy, -cz>(), MC.wr * S.ld<D, 0, 0, 0>());
+  const float2 bDcL = fma2(MC.wl, S.ld<AB + D, -cx, -cy, -cz>(), MC.wr * S.ld<AB + D, 0, 0, 0>());
   const float2 bCm = S.ld<AB + C, -dx, -dy, -dz>(), aCm = S.ld<C, -dx, -dy, -dz>();
-  const float2 aCdL = MD.wl * aCm + MD.wr * aH;
-  const float2 bCdL = MD.wl * bCm + MD.wr * bH;
-  const float2 fLo = aDcL * bCdL + bDcL * aCdL;
+  const float2 aCdL = fma2(MD.wl, aCm, MD.wr * aH);
+  const float2 bCdL = fma2(MD.wl, bCm, MD.wr * bH);
+  const float2 fLo = fma2(aDcL, bCdL, bDcL * aCdL);
   const float2 gLo = (bH - bCm) * MD.ic;
   // high face
-  const float2 aDcH = MC.wl * S.ld<D, dx - cx, dy - cy, dz - cz>() + MC.wr * S.ld<D, dx, dy, dz>();
-  const float2 bDcH = MC.wl * S.ld<AB + D, dx - cx, dy - cy, dz - cz>() + MC.wr * S.ld<AB + D, dx, dy, dz>();
+  const float2 aDcH = fma2(MC.wl, S.ld<D, dx - cx, dy - cy, dz - cz>(), MC.wr * S.ld<D, dx, dy, dz>());
+  const float2 bDcH = fma2(MC.wl, S.ld<AB + D, dx - cx, dy - cy, dz - cz>(), MC.wr * S.ld<AB + D, dx, dy, dz>());
   const float2 bCp = S.ld<AB + C, dx, dy, dz>(), aCp = S.ld<C, dx, dy, dz>();
-  const float2 aCdH = MD.wlp * aH + MD.wrp * aCp;
-  const float2 bCdH = MD.wlp * bH + MD.wrp * bCp;
-  const float2 fHi = aDcH * bCdH + bDcH * aCdH;
+  const float2 aCdH = fma2(MD.wlp, aH, MD.wrp * aCp);
+  const float2 bCdH = fma2(MD.wlp, bH, MD.wrp * bCp);
+  const float2 fHi = fma2(aDcH, bCdH, bDcH * aCdH);
   const float2 gHi = (bCp - bH) * MD.icp;
-  conv += (fHi - fLo) * MD.ix;
-  lap += (gHi - gLo) * MD.ix;
+  conv = fma2(fHi - fLo, MD.ix, conv);
+  lap = fma2(gHi - gLo, MD.ix, lap);
 }
 
 // Momentum component C: conv = S(q, v) (symmetrised convective form), lap = Lap v
 template <int C>
-__device__ __forceinline__ void momentum_pair(const Ring2& S, const Bundle<float2>& mx, const Bundle<float>& my,
-                                              const Bundle<float>& mz, float2& conv, float2& lap) {
+__device__ __forceinline__ void momentum_pair(const Ring2& S, const Bundle<float2>& mx, const Bundle<float2>& my,
+                                              const Bundle<float2>& mz, float2& conv, float2& lap) {
   constexpr int cx = unit_(C, 0), cy = unit_(C, 1), cz = unit_(C, 2);
   constexpr int AB = 4;
   const auto& MC = pick<C>(mx, my, mz);
   const float2 aH = S.ld<C, 0, 0, 0>(), bH = S.ld<AB + C, 0, 0, 0>();
   const float2 aM = S.ld<C, -cx, -cy, -cz>(), bM = S.ld<AB + C, -cx, -cy, -cz>();
   const float2 aP = S.ld<C, cx, cy, cz>(), bP = S.ld<AB + C, cx, cy, cz>();
-  const float2 aE = 0.5f * (aH + aP), bE = 0.5f * (bH + bP);
-  const float2 aW = 0.5f * (aM + aH), bW = 0.5f * (bM + bH);
-  conv = 2.f * (aE * bE - aW * bW) * MC.ic;
+  const float2 half = bc(0.5f), two = bc(2.f);
+  const float2 aE = half * (aH + aP), bE = half * (bH + bP);
+  const float2 aW = half * (aM + aH), bW = half * (bM + bH);
+  conv = two * (aE * bE - aW * bW) * MC.ic;
   lap = ((bP - bH) * MC.ix - (bH - bM) * MC.ixm) * MC.ic;
   constexpr int D1 = (C + 1) % 3, D2 = (C + 2) % 3;
   transverse<C, D1>(S, MC, pick<D1>(mx, my, mz), aH, bH, conv, lap);
@@ -147,20 +188,21 @@ __device__ __forceinline__ void temperature_dir(const Ring2& S, const BD& MD, fl
   constexpr int dx = unit_(D, 0), dy = unit_(D, 1), dz = unit_(D, 2);
   constexpr int AB = 4;
   const float2 Tam = S.ld<3, -dx, -dy, -dz>(), Tbm = S.ld<AB + 3, -dx, -dy, -dz>();
-  const float2 fLo = S.ld<D, 0, 0, 0>() * (MD.wl * Tbm + MD.wr * TbH) + S.ld<AB + D, 0, 0, 0>() * (MD.wl * Tam + MD.wr * TaH);
+  const float2 fLo = fma2(S.ld<D, 0, 0, 0>(), fma2(MD.wl, Tbm, MD.wr * TbH),
+                          S.ld<AB + D, 0, 0, 0>() * fma2(MD.wl, Tam, MD.wr * TaH));
   float2 gLo = (TbH - Tbm) * MD.ic;
   const float2 Tap = S.ld<3, dx, dy, dz>(), Tbp = S.ld<AB + 3, dx, dy, dz>();
-  const float2 fHi = S.ld<D, dx, dy, dz>() * (MD.wlp * TbH + MD.wrp * Tbp) +
-                     S.ld<AB + D, dx, dy, dz>() * (MD.wlp * TaH + MD.wrp * Tap);
+  const float2 fHi = fma2(S.ld<D, dx, dy, dz>(), fma2(MD.wlp, TbH, MD.wrp * Tbp),
+                          S.ld<AB + D, dx, dy, dz>() * fma2(MD.wlp, TaH, MD.wrp * Tap));
   float2 gHi = (Tbp - TbH) * MD.icp;
   if (!lo_in) gLo = make_float2(0.f, 0.f);
   if (!hi_in) gHi = make_float2(0.f, 0.f);
-  conv += (fHi - fLo) * MD.ix;
-  lap += (gHi - gLo) * MD.ix;
+  conv = fma2(fHi - fLo, MD.ix, conv);
+  lap = fma2(gHi - gLo, MD.ix, lap);
 }
 
-__device__ __forceinline__ void temperature_pair(const Ring2& S, const Bundle<float2>& mx, const Bundle<float>& my,
-                                                 const Bundle<float>& mz, int j, int ny, int k, int nz, float2& conv,
+__device__ __forceinline__ void temperature_pair(const Ring2& S, const Bundle<float2>& mx, const Bundle<float2>& my,
+                                                 const Bundle<float2>& mz, int j, int ny, int k, int nz, float2& conv,
                                                  float2& lap) {
   const float2 TaH = S.ld<3, 0, 0, 0>(), TbH = S.ld<4 + 3, 0, 0, 0>();
   conv = make_float2(0.f, 0.f);
@@ -247,26 +289,27 @@ __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
   const int x = i0 + 2 * tx, j = j0 + ty;
   const bool active = (x < nx && j < ny);  // nx is a multiple of kPX: both cells are in the domain
   const Bundle<float2> mx = load_bundle_pair(g, active ? x : 0);
-  const Bundle<float> my = load_bundle(g, 1, active ? j : 0);
+  const Bundle<float2> my = broadcast(load_bundle(g, 1, active ? j : 0));
   for (int k = k0; k < kend; ++k) {
     if (k + 2 <= kend) issue_plane(k + 2);  // plane k+2 feeds the output plane k+1
     const bool ready = wait_plane(k + 1) && ok;
     if (active && ready) {
-      const Bundle<float> mz = load_bundle(g, 2, k);
+      const Bundle<float2> mz = broadcast(load_bundle(g, 2, k));
       Ring2 S;
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz)
         S.p[dz + 1] = sm + ((k + dz + kPRing) % kPRing) * kPNA * kPL2 + (ty + 1) * kPW2 + (2 * tx + kPX0);
       float2 conv, lap;
       momentum_pair<0>(S, mx, my, mz, conv, lap);
-      float2 r0 = lap - conv - sigma * S.ld<4, 0, 0, 0>();
+      const float2 msig = bc(-sigma);
+      float2 r0 = fma2(msig, S.ld<4, 0, 0, 0>(), lap - conv);
       momentum_pair<1>(S, mx, my, mz, conv, lap);
-      const float2 r1 = lap - conv - sigma * S.ld<5, 0, 0, 0>();
+      const float2 r1 = fma2(msig, S.ld<5, 0, 0, 0>(), lap - conv);
       momentum_pair<2>(S, mx, my, mz, conv, lap);
-      const float2 Tf = mz.wl * S.ld<7, 0, 0, -1>() + mz.wr * S.ld<7, 0, 0, 0>();
-      const float2 r2 = lap - conv + Gr * Tf - sigma * S.ld<6, 0, 0, 0>();
+      const float2 Tf = fma2(mz.wl, S.ld<7, 0, 0, -1>(), mz.wr * S.ld<7, 0, 0, 0>());
+      const float2 r2 = fma2(msig, S.ld<6, 0, 0, 0>(), fma2(bc(Gr), Tf, lap - conv));
       temperature_pair(S, mx, my, mz, j, ny, k, nz, conv, lap);
-      const float2 r3 = lap * invPr - conv - sigma * S.ld<7, 0, 0, 0>();
+      const float2 r3 = fma2(msig, S.ld<7, 0, 0, 0>(), lap * bc(invPr) - conv);
       const int o = (k * ny + j) * nx + x;
       if (x == 0) r0.x = 0.f;  // the x = 0 wall slot of u
       const float2 zero = make_float2(0.f, 0.f);
