@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(256) k_divergence4(Geo<float> g, int N, const 
   }
   const int ob = act ? (k0 * ny + j) * nx + i0 : 0;
   float4 wlo = (act && k0 >= 1) ? ldg4(W, ob) : zero4();
+#pragma unroll
   for (int k = k0; k < k1; ++k) {
     const int o = ob + (k - k0) * pl;
     const float4 u = act ? ldg4(U, o) : zero4();

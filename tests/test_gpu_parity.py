@@ -66,7 +66,7 @@ def round32(api):
 
 
 GRIDS = [((7, 5, 3), 0.0), ((17, 13, 11), 1.5), ((32, 32, 32), 1.5), ((2, 2, 2), 0.0), ((64, 48, 40), 1.5),
-         ((130, 3, 5), 0.0)]
+         ((130, 3, 5), 0.0), ((128, 16, 20), 0.0), ((192, 17, 35), 1.5)]
 
 
 @pytest.mark.parametrize("shape,stretch", GRIDS)
