@@ -1205,20 +1205,29 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     ++mv;
     const R* yp = in;
     R* yc = y0.p;
+    // range check of the recurrence every `chk` steps on the norm its correction pass sums (FP32 data
+    // overflows near 3e38: a polynomial that amplifies an outlier strongly can get there within 16 steps)
+    const int chk = std::is_same<R, double>::value ? 16 : 4;
+    const double big = std::is_same<R, double>::value ? 1e30 : 1e15;
     for (int j = 1; j < filt.deg; ++j) {
       const double tn = 1.0 / (2.0 * s - filt.c2 * tau);
       R* dst = (yp == in) ? y1.p : const_cast<R*>(yp);  // y_{j+1} overwrites y_{j-1} (never the input)
+      const bool check = (j % chk == 0);
       FV_TRY(chebyshev_step<R>(g, Gr, sigma, q, yc, yp, 2.0 * tn, 2.0 * tn * (sigma - filt.d), -filt.c2 * tau * tn,
-                               dst));
+                               dst, check ? 0 : -1));
       ++mv;
       yp = yc;
       yc = dst;
       tau = tn;
-      if (j % 16 == 0) {  // keep both terms of the recurrence in range (yp is scratch by now)
+      if (check) {  // keep both terms of the recurrence in range (yp is scratch by now)
         double nn;
-        FV_TRY(V.dot(yc, yc, &nn));
+        FV_TRY(read_scalars(g, 0, 1, &nn));
+        if (!std::isfinite(nn)) {
+          set_error("non-finite Chebyshev recurrence");
+          return FV_ENAN;
+        }
         nn = std::sqrt(nn);
-        if (nn > 1e30 || nn < 1e-30) {
+        if (nn > big || nn < 1.0 / big) {
           FV_TRY(V.lin(yc, {{1.0 / nn, yc}}));
           FV_TRY(V.lin(const_cast<R*>(yp), {{1.0 / nn, yp}}));
         }
