@@ -149,6 +149,19 @@ int fv_dot_noalloc(int prec, long long n, const void* a, const void* b, double* 
 
 /* y <- alpha x + beta y over 4N elements (coefficients applied in FP64). */
 int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y);
+/* Batched fused hot path: W_i = P (J(q) V_i - sigma V_i) + sigma V_i for the
+ * nvec vectors stored one after another in V and W (device, nvec * 4N
+ * elements each, precision `prec`).  use_graph = 1: the launch sequence of the
+ * whole block is captured once into a CUDA graph (on a private stream; the
+ * first call with a new argument set runs eagerly and captures) and replayed
+ * on the handle's stream by later calls with the same q, V, W, nvec, Gr and
+ * sigma, which removes the per-kernel launch cost that dominates small grids.
+ * The paper has no batched form; it is the building block of applying many
+ * Krylov vectors or several problems per launch.  W must not overlap V or q.
+ * Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
+int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
+                         void* W, int use_graph);
+
 /* out = L^-1 in, where L is the diffusion part of J (Eqs. 1-2 with homogeneous wall data): per
  * velocity component the Laplacian with no-slip walls, for T the Laplacian / Pr with T = 0 at the
  * x-walls (Eq. 4) and zero flux at the others (Eqs. 5-6).  Separable on the tensor-product grid, so

@@ -689,6 +689,8 @@ int fv_grid_destroy(fv_grid g) {
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
   if (g->tc.buf) cudaFree(g->tc.buf);
   if (g->ws.err) cudaFree(g->ws.err);
+  if (g->batch_exec) cudaGraphExecDestroy(g->batch_exec);
+  if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
   delete g;
   return FV_OK;
 }
@@ -747,6 +749,78 @@ int fv_project(fv_grid g, int prec, void* v, int max_it, double tol, int* iters,
   if (prec == FV_FP64) return project_inplace<double>(g, (double*)v, max_it, tol, iters, div_rel);
   if (prec == FV_FP32) return project_inplace<float>(g, (float*)v, max_it, tol, iters, div_rel);
   return invalid("precision must be FV_FP64 or FV_FP32");
+}
+
+extern "C++" {
+// nvec fused J.v + projections, vector i at offset i * 4N of V and W
+template <typename R>
+static int batch_launches(fv_grid_s* g, double Gr, double sigma, const R* q, int nvec, const R* V, R* W) {
+  const size_t n = 4 * g->N;
+  for (int i = 0; i < nvec; ++i) FV_TRY(jvp_project<R>(g, Gr, sigma, q, V + (size_t)i * n, W + (size_t)i * n));
+  return FV_OK;
+}
+}
+
+int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
+                         void* W, int use_graph) {
+  if (!g || !q || !V || !W) return invalid("null argument");
+  if (nvec < 1) return invalid("nvec must be at least 1");
+  if (prec != FV_FP64 && prec != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
+  const size_t bytes = 4 * g->N * (prec == FV_FP64 ? 8 : 4) * (size_t)nvec;
+  const char *v0 = (const char*)V, *w0 = (const char*)W;
+  if ((w0 < v0 + bytes && v0 < w0 + bytes) || (const char*)q == w0) return invalid("W must not overlap V or q");
+  auto launches = [&]() -> int {
+    return prec == FV_FP64 ? batch_launches<double>(g, Gr, sigma, (const double*)q, nvec, (const double*)V, (double*)W)
+                           : batch_launches<float>(g, Gr, sigma, (const float*)q, nvec, (const float*)V, (float*)W);
+  };
+  if (!use_graph) return launches();
+  // first call: workspace, function attributes and tensor-core set-up happen outside the capture
+  if (prec == FV_FP64)
+    FV_TRY(ensure_ws<double>(g));
+  else
+    FV_TRY(ensure_ws<float>(g));
+  fv_grid_s::BatchKey key;
+  key.prec = prec;
+  key.nvec = nvec;
+  key.Gr = Gr;
+  key.sigma = sigma;
+  key.q = q;
+  key.V = V;
+  key.W = W;
+  if (!(g->batch_exec && key == g->batch_key)) {
+    if (g->batch_exec) {
+      cudaGraphExecDestroy(g->batch_exec);
+      g->batch_exec = nullptr;
+    }
+    // one eager pass first (kernel attributes are set on first use, which capture does not allow)
+    FV_TRY(launches());
+    if (!g->capture_stream) FV_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    cudaStream_t user = g->stream;
+    const bool prof = g->prof.enabled;
+    g->prof.enabled = false;
+    g->stream = g->capture_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
+    int st = (e == cudaSuccess) ? launches() : cuda_status(e, "cudaStreamBeginCapture");
+    const cudaError_t e2 = cudaStreamEndCapture(g->capture_stream, &graph);
+    g->stream = user;
+    g->prof.enabled = prof;
+    if (st == FV_OK && e2 != cudaSuccess) st = cuda_status(e2, "cudaStreamEndCapture");
+    if (st == FV_OK) {
+      const cudaError_t e3 = cudaGraphInstantiate(&g->batch_exec, graph, 0);
+      if (e3 != cudaSuccess) st = cuda_status(e3, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != FV_OK) {
+      g->batch_exec = nullptr;
+      return st;
+    }
+    g->batch_key = key;
+    return FV_OK;  // the eager pass above already produced W
+  }
+  FV_CUDA(cudaGraphLaunch(g->batch_exec, g->stream));
+  return FV_OK;
 }
 
 int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out) {

@@ -92,6 +92,18 @@ struct fv_grid_s {
   double min_width[3];
   mutable fv::Profiler prof;
   fv::TcState tc;
+  // batched J.v + projection: the captured launch sequence of the last argument set, replayed while the
+  // arguments stay the same, and the private stream it is captured on
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  struct BatchKey {
+    int prec = -1, nvec = 0;
+    double Gr = 0.0, sigma = 0.0;
+    const void *q = nullptr, *V = nullptr, *W = nullptr;
+    bool operator==(const BatchKey& o) const {
+      return prec == o.prec && nvec == o.nvec && Gr == o.Gr && sigma == o.sigma && q == o.q && V == o.V && W == o.W;
+    }
+  } batch_key;
 };
 
 namespace fv {

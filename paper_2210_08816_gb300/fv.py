@@ -83,6 +83,7 @@ def lib():
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
             "fv_convert": (i, [vp, i, vp, vp]),
             "fv_diffusion_solve": (i, [vp, i, vp, vp]),
+            "fv_jvp_project_batch": (i, [vp, i, d, d, vp, i, vp, vp, i]),
             "fv_newton_default_opts": (None, [C.POINTER(fv_newton_opts)]),
             "newton_steady": (i, [vp, d, vp, C.POINTER(fv_newton_opts), C.POINTER(fv_newton_report)]),
             "fv_arnoldi_default_opts": (None, [C.POINTER(fv_arnoldi_opts)]),
@@ -102,7 +103,7 @@ def lib():
 
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
-            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve",
+            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
             "fv_newton_default_opts",
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
@@ -198,6 +199,15 @@ def fv_project(g: Grid, prec, v, max_it=1, tol=0.0, want_div=False):
     _check(lib().fv_project(g.h, prec, _ptr(v, g.dtype(prec), g.n, "v"), int(max_it), float(tol), C.byref(it),
                             C.byref(dv) if want_div else None), "fv_project")
     return it.value, (dv.value if want_div else None)
+
+
+def fv_jvp_project_batch(g: Grid, prec, Gr, sigma, q, V, W, nvec, use_graph=False):
+    """W_i = P (J V_i - sigma V_i) + sigma V_i for nvec vectors stored back to back in V and W."""
+    dt = g.dtype(prec)
+    _check(lib().fv_jvp_project_batch(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"), int(nvec),
+                                      _ptr(V, dt, g.n * nvec, "V"), _ptr(W, dt, g.n * nvec, "W"),
+                                      1 if use_graph else 0), "fv_jvp_project_batch")
+    return W
 
 
 def fv_diffusion_solve(g: Grid, prec, x, out):

@@ -255,3 +255,38 @@ def test_stream_ordered_step_matches_the_synchronous_one(fv):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     assert float(n2.item()) == nrm
+
+
+@pytest.mark.parametrize("prec_name,shape", [("fp32", (64, 48, 40)), ("fp64", (17, 13, 11))])
+def test_batched_fused_path_eager_and_graph(fv, prec_name, shape):
+    """fv_jvp_project_batch gives exactly the per-vector fv_jvp_project results, eagerly and through its
+    captured graph (first call captures, later calls replay it on new vector contents)."""
+    prec = fv.FV_FP32 if prec_name == "fp32" else fv.FV_FP64
+    dt = torch.float32 if prec_name == "fp32" else torch.float64
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    nvec, Gr, sigma = 5, 3e5, -60.0
+    q = dev(state(og, 21), dt)
+    V = torch.cat([dev(vector(og, 30 + i), dt) for i in range(nvec)])
+    ref = torch.empty_like(V)
+    for i in range(nvec):
+        fv.fv_jvp_project(g, prec, Gr, sigma, q, V[i * g.n:(i + 1) * g.n], ref[i * g.n:(i + 1) * g.n])
+    W = torch.empty_like(V)
+    fv.fv_jvp_project_batch(g, prec, Gr, sigma, q, V, W, nvec, use_graph=False)
+    assert torch.equal(W, ref)
+    for _ in range(2):  # capture, then replay
+        W.zero_()
+        fv.fv_jvp_project_batch(g, prec, Gr, sigma, q, V, W, nvec, use_graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(W, ref)
+    # the replay reads the vectors' current contents
+    V.mul_(2.0)
+    fv.fv_jvp_project_batch(g, prec, Gr, sigma, q, V, W, nvec, use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(W, 2.0 * ref, rtol=1e-5 if prec_name == "fp32" else 1e-12, atol=0)
+    # a different argument set is captured anew
+    fv.fv_jvp_project_batch(g, prec, 2 * Gr, sigma, q, V, W, nvec, use_graph=True)
+    torch.cuda.synchronize()
+    ref2 = torch.empty_like(V[:g.n])
+    fv.fv_jvp_project(g, prec, 2 * Gr, sigma, q, V[:g.n], ref2)
+    assert torch.equal(W[:g.n], ref2)
