@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--no-eigen", action="store_true", help="skip the 32^3 time-to-eigenpair leg")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched (block of 16 vectors) leg")
     p.add_argument("--cpu-sample-only", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -401,6 +402,8 @@ def finish(args, ws, rank, n, value, K, W, ms_step, e2e, launches, roof, hbm_ste
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_eigen:
         result["time_to_eigenpair"] = eigen_leg(fv, device)
+    if rank == 0 and not args.no_batch:
+        result["batched"] = batch_leg(fv, device)
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(n)
     return result
@@ -424,6 +427,42 @@ def measured_traffic(kind, n):
     if sha != rec.get("sha") or rec.get("grid") != n:
         return None
     return rec.get("bytes_per_launch")
+
+
+def batch_leg(fv, device, reps=10):
+    """Blocks of 16 FP32 N(0,1) vectors through fv_jvp_project_batch on stretched grids of the batched
+    workload's sizes and Gr points (64^3 at 3e7, 100^3 at 7.44e7, 128^3 at 2.5e8; base state: conduction
+    plus a seeded projected perturbation), eager launches against the captured CUDA graph."""
+    import torch
+    out = {"workload": "blocks of 16 FP32 N(0,1) vectors, J.v+projection each", "unit": "J.v+projection/s"}
+    for n, gr in ((64, 3.0e7), (100, 7.44e7), (128, 2.5e8)):
+        g, q64, _, _ = make_inputs(n, device)
+        q = q64.float()
+        nvec = 16
+        gen = torch.Generator(device=device).manual_seed(100 + n)
+        V = torch.randn(nvec * g.n, generator=gen, device=device, dtype=torch.float32)
+        for i in range(nvec):
+            fv.fv_project(g, fv.FV_FP32, V[i * g.n:(i + 1) * g.n])
+        W = torch.empty_like(V)
+        sig = -0.5 * (1.0 / PR) * 3 * 4.0 / (min(b - a for a, b in zip(g_faces(n)[:-1], g_faces(n)[1:])) ** 2)
+        row = {}
+        for name, graph in (("eager", False), ("graph", True)):
+            for _ in range(2):
+                fv.fv_jvp_project_batch(g, fv.FV_FP32, gr, sig, q, V, W, nvec, use_graph=graph)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fv.fv_jvp_project_batch(g, fv.FV_FP32, gr, sig, q, V, W, nvec, use_graph=graph)
+            e1.record()
+            e1.synchronize()
+            row[name] = round(reps * nvec / (e0.elapsed_time(e1) / 1e3), 1)
+        row["graph_speedup"] = round(row["graph"] / row["eager"], 3)
+        out[f"{n}^3 Gr={gr:g}"] = row
+        g.close()
+        del V, W, q, q64
+        torch.cuda.empty_cache()
+    return out
 
 
 def eigen_leg(fv, device):
