@@ -434,39 +434,69 @@ def measured_traffic(kind, n):
     return rec.get("bytes_per_launch")
 
 
-def batch_leg(fv, device, reps=10):
-    """Blocks of 16 FP32 N(0,1) vectors through fv_jvp_project_batch on stretched grids of the batched
-    workload's sizes and Gr points (64^3 at 3e7, 100^3 at 7.44e7, 128^3 at 2.5e8; base state: conduction
-    plus a seeded projected perturbation), eager launches against the captured CUDA graph."""
+BATCH_POINTS = ((64, 3.0e7), (64, 4.06e7), (64, 5.50e7), (64, 7.44e7), (100, 1.01e8), (100, 1.36e8),
+                (128, 1.85e8), (128, 2.5e8))
+
+
+def batch_leg(fv, device, reps=10, nvec=16):
+    """The batched workload: 8 continuation points, Gr log-spaced 3e7 .. 2.5e8, on stretched grids 4 x 64^3,
+    2 x 100^3, 2 x 128^3, each applying a block of 16 seeded FP32 N(0,1) vectors (projected) through
+    J.v + projection.  Base state per grid: conduction plus a seeded projected perturbation.
+    Per grid size (first point of that size): 16 single-vector fv_jvp_project calls ("loop") against the
+    block path eager and graph-replayed (z-chunk autotuned).  Then all 8 problems in ONE captured graph
+    with concurrent branches (fv_batch_plan): 128 J.v + projections per replay."""
     import torch
-    out = {"workload": "blocks of 16 FP32 N(0,1) vectors, J.v+projection each", "unit": "J.v+projection/s"}
-    for n, gr in ((64, 3.0e7), (100, 7.44e7), (128, 2.5e8)):
+    out = {"workload": "8 continuation points (Gr 3e7..2.5e8 log-spaced; 4 x 64^3, 2 x 100^3, 2 x 128^3 stretched), "
+                       "blocks of 16 FP32 N(0,1) vectors, J.v+projection each", "unit": "J.v+projection/s"}
+
+    def timed(fn, count):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return round(reps * count / (e0.elapsed_time(e1) / 1e3), 1)
+
+    probs, seen = [], set()
+    for k, (n, gr) in enumerate(BATCH_POINTS):
         g, q64, _, _ = make_inputs(n, device)
         q = q64.float()
-        nvec = 16
-        gen = torch.Generator(device=device).manual_seed(100 + n)
+        del q64
+        gen = torch.Generator(device=device).manual_seed(100 + k)
         V = torch.randn(nvec * g.n, generator=gen, device=device, dtype=torch.float32)
         for i in range(nvec):
             fv.fv_project(g, fv.FV_FP32, V[i * g.n:(i + 1) * g.n])
         W = torch.empty_like(V)
         sig = -0.5 * (1.0 / PR) * 3 * 4.0 / (min(b - a for a, b in zip(g_faces(n)[:-1], g_faces(n)[1:])) ** 2)
-        row = {}
-        for name, graph in (("eager", False), ("graph", True)):
-            for _ in range(2):
-                fv.fv_jvp_project_batch(g, fv.FV_FP32, gr, sig, q, V, W, nvec, use_graph=graph)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                fv.fv_jvp_project_batch(g, fv.FV_FP32, gr, sig, q, V, W, nvec, use_graph=graph)
-            e1.record()
-            e1.synchronize()
-            row[name] = round(reps * nvec / (e0.elapsed_time(e1) / 1e3), 1)
-        row["graph_speedup"] = round(row["graph"] / row["eager"], 3)
+        probs.append((g, gr, sig, q, V, W, nvec))
+        if n in seen:
+            continue
+        seen.add(n)
+
+        def loop():
+            for i in range(nvec):
+                fv.fv_jvp_project(g, fv.FV_FP32, gr, sig, q, V[i * g.n:(i + 1) * g.n], W[i * g.n:(i + 1) * g.n])
+
+        row = {"loop": timed(loop, nvec)}
+        for name, graph in (("block_eager", False), ("block_graph", True)):
+            row[name] = timed(lambda: fv.fv_jvp_project_batch(g, fv.FV_FP32, gr, sig, q, V, W, nvec,
+                                                              use_graph=graph, autotune=True), nvec)
+        row["zchunk"] = fv.fv_get_tuning(g)[0]
+        row["block_graph_vs_loop"] = round(row["block_graph"] / row["loop"], 3)
         out[f"{n}^3 Gr={gr:g}"] = row
-        g.close()
-        del V, W, q, q64
-        torch.cuda.empty_cache()
+    plan = fv.BatchPlan(probs, fv.FV_FP32, autotune=True)
+    stream = torch.cuda.current_stream().cuda_stream
+    total = sum(p[6] for p in probs)
+    out["one_graph_8_points"] = {"value": timed(lambda: plan.launch(stream), total), "products_per_replay": total}
+    plan.close()
+    for p in probs:
+        p[0].close()
+    del probs
+    torch.cuda.empty_cache()
     return out
 
 

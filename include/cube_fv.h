@@ -149,18 +149,53 @@ int fv_dot_noalloc(int prec, long long n, const void* a, const void* b, double* 
 
 /* y <- alpha x + beta y over 4N elements (coefficients applied in FP64). */
 int fv_axpby(fv_grid g, int prec, double alpha, const void* x, double beta, void* y);
+/* Flags of the block calls below. */
+enum { FV_BATCH_GRAPH = 1, FV_BATCH_AUTOTUNE = 2 };
+
 /* Batched fused hot path: W_i = P (J(q) V_i - sigma V_i) + sigma V_i for the
  * nvec vectors stored one after another in V and W (device, nvec * 4N
- * elements each, precision `prec`).  use_graph = 1: the launch sequence of the
- * whole block is captured once into a CUDA graph (on a private stream; the
- * first call with a new argument set runs eagerly and captures) and replayed
- * on the handle's stream by later calls with the same q, V, W, nvec, Gr and
- * sigma, which removes the per-kernel launch cost that dominates small grids.
- * The paper has no batched form; it is the building block of applying many
- * Krylov vectors or several problems per launch.  W must not overlap V or q.
- * Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
+ * elements each, precision `prec`).  Each stage runs as ONE launch over the
+ * whole block where its kernel has a block form (FP32: the two-cell J.v
+ * stencil for nx % 64 == 0, the divergence and correction for nx % 4 == 0;
+ * both precisions: the six pressure-solve passes), else one launch per vector.
+ * Block buffers (nvec * 6N elements) are owned by the handle and grown on
+ * demand.  flags:
+ *   FV_BATCH_AUTOTUNE: before the first block of a new size, time each z-chunk
+ *     of the block stencil (4 ... 64 planes per CTA) with CUDA events on the
+ *     handle's stream and keep the fastest for later blocks (fv_get_tuning);
+ *   FV_BATCH_GRAPH: the block's launch sequence is captured once into a CUDA
+ *     graph (on a private stream; the first call with a new argument set runs
+ *     eagerly and captures) and replayed on the handle's stream by later calls
+ *     with the same q, V, W, nvec, Gr and sigma.
+ * The paper has no batched form (Krylov vectors are applied one at a time in
+ * Section 1's methods); blocks of vectors and of continuation points (Section
+ * 4.2's Gr sweeps) are how the same products fill one GPU.  W must not overlap
+ * V or q.  Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
 int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
-                         void* W, int use_graph);
+                         void* W, int flags);
+
+/* The block stencil's z-chunk picked by the autotuner (0 = not tuned: the
+ * built-in 32 planes) and the block size it was timed on. */
+int fv_get_tuning(fv_grid g, int* pair_zchunk, int* tuned_nvec);
+
+/* Several problems (e.g. continuation points at different Gr on grids of
+ * different sizes), each a block as in fv_jvp_project_batch, captured into ONE
+ * CUDA graph whose branches run concurrently.  Problem i: handle grids[i]
+ * (distinct handles: their workspaces run at the same time), Gr[i], sigma[i],
+ * base state q[i], nvec[i] vectors V[i] -> W[i] (device, layouts as above, all
+ * of precision `prec`).  Creation runs every block once eagerly (W is written)
+ * and captures; fv_batch_plan_launch replays the graph on `stream` (a
+ * cudaStream_t; NULL = legacy default).  The plan stores the pointers: the
+ * buffers and the handles must outlive it, and a later fv_jvp_project_batch
+ * call that grows a handle's block buffers invalidates it (launch then
+ * returns FV_EINVAL).  flags: FV_BATCH_AUTOTUNE as above.  Errors: FV_EINVAL,
+ * FV_ECUDA, FV_ENOMEM. */
+typedef struct fv_batch_plan_s* fv_batch_plan;
+int fv_batch_plan_create(int nprob, const fv_grid* grids, int prec, const double* Gr, const double* sigma,
+                         const void* const* q, const int* nvec, const void* const* V, void* const* W, int flags,
+                         fv_batch_plan* out);
+int fv_batch_plan_launch(fv_batch_plan plan, void* stream);
+int fv_batch_plan_destroy(fv_batch_plan plan);
 
 /* out = L^-1 in, where L is the diffusion part of J (Eqs. 1-2 with homogeneous wall data): per
  * velocity component the Laplacian with no-slip walls, for T the Laplacian / Pr with T = 0 at the

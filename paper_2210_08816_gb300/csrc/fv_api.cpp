@@ -22,6 +22,7 @@ int cuda_status(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return FV_ECUDA;
 }
+static int cu_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? FV_OK : cuda_status(e, what); }
 static int invalid(const std::string& msg) {
   set_error(msg);
   return FV_EINVAL;
@@ -682,6 +683,9 @@ int fv_grid_destroy(fv_grid g) {
     if (g->ws.Y[p]) cudaFree(g->ws.Y[p]);
     if (g->ws.t0[p]) cudaFree(g->ws.t0[p]);
     if (g->ws.t1[p]) cudaFree(g->ws.t1[p]);
+    if (g->ws.bY[p]) cudaFree(g->ws.bY[p]);
+    if (g->ws.bt0[p]) cudaFree(g->ws.bt0[p]);
+    if (g->ws.bt1[p]) cudaFree(g->ws.bt1[p]);
   }
   if (g->ws.partials) cudaFree(g->ws.partials);
   if (g->ws.scalars) cudaFree(g->ws.scalars);
@@ -752,33 +756,154 @@ int fv_project(fv_grid g, int prec, void* v, int max_it, double tol, int* iters,
 }
 
 extern "C++" {
-// nvec fused J.v + projections, vector i at offset i * 4N of V and W
+// block buffers for nvec vectors; a reallocation drops the handle's captured block (it refers to them)
 template <typename R>
-static int batch_launches(fv_grid_s* g, double Gr, double sigma, const R* q, int nvec, const R* V, R* W) {
-  const size_t n = 4 * g->N;
-  for (int i = 0; i < nvec; ++i) FV_TRY(jvp_project<R>(g, Gr, sigma, q, V + (size_t)i * n, W + (size_t)i * n));
+static int ensure_batch_ws(fv_grid_s* g, int nvec) {
+  const int p = prec_index<R>();
+  if (g->ws.bcap[p] >= nvec) return FV_OK;
+  if (g->batch_exec) {
+    cudaGraphExecDestroy(g->batch_exec);
+    g->batch_exec = nullptr;
+    g->batch_key = fv_grid_s::BatchKey();
+  }
+  void** bufs[3] = {&g->ws.bY[p], &g->ws.bt0[p], &g->ws.bt1[p]};
+  for (void** b : bufs)
+    if (*b) {
+      cudaFree(*b);
+      *b = nullptr;
+    }
+  g->ws.bcap[p] = 0;
+  ++g->ws.bgen;
+  const size_t N = g->N;
+  const size_t sizes[3] = {4 * N * nvec * sizeof(R), N * nvec * sizeof(R), N * nvec * sizeof(R)};
+  for (int i = 0; i < 3; ++i)
+    if (cudaMalloc(bufs[i], sizes[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (void** b : bufs)
+        if (*b) {
+          cudaFree(*b);
+          *b = nullptr;
+        }
+      set_error("block workspace allocation failed");
+      return FV_ENOMEM;
+    }
+  g->ws.bcap[p] = nvec;
   return FV_OK;
+}
+
+// nvec fused J.v + projections, vector i at offset i * 4N of V and W: every stage is one launch over the
+// whole block where its kernel has a block form (two-cell stencil, quad divergence and correction, all
+// pressure-solve passes), else one launch per vector
+template <typename R>
+static int jvp_project_block(fv_grid_s* g, double Gr, double sigma, const R* q, int nvec, const R* V, R* W) {
+  FV_TRY(ensure_ws<R>(g));
+  FV_TRY(ensure_batch_ws<R>(g, nvec));
+  const int p = prec_index<R>();
+  R* Y = (R*)g->ws.bY[p];
+  R* phi = (R*)g->ws.bt1[p];
+  R* tmp = (R*)g->ws.bt0[p];
+  const size_t n4 = 4 * g->N;
+  bool pair = false;
+  if constexpr (sizeof(R) == 4) pair = stencil_pair_eligible(g, q, V);
+  if constexpr (sizeof(R) == 4) {
+    if (pair) FV_TRY(launch_stencil_pair(g, Gr, sigma, q, V, Y, nvec));
+  }
+  if (!pair)
+    for (int i = 0; i < nvec; ++i) FV_TRY(launch_jvp<R>(g, Gr, sigma, q, V + i * n4, Y + i * n4));
+  FV_TRY(launch_divergence<R>(g, Y, phi, nvec));
+  FV_TRY(launch_poisson_block<R>(g, phi, phi, tmp, nvec));
+  FV_TRY(launch_correct_block<R>(g, Y, phi, sigma != 0.0 ? V : nullptr, sigma, W, nvec));
+  return FV_OK;
+}
+
+// Autotuner of the block stencil's z-chunk: every candidate is timed with CUDA events on the handle's
+// stream (one warm-up launch, then three) over the block it will run on; the fastest is kept.
+static int autotune_pair(fv_grid_s* g, double Gr, double sigma, const float* q, int nvec, const float* V) {
+  if (nvec < 2 || !stencil_pair_eligible(g, q, V) || g->tune.pair_zc_nvec == nvec) return FV_OK;
+  FV_TRY(ensure_batch_ws<float>(g, nvec));
+  float* Y = (float*)g->ws.bY[1];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FV_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_status(cudaErrorMemoryAllocation, "cudaEventCreate");
+  }
+  const bool prof = g->prof.enabled;
+  g->prof.enabled = false;
+  int st = FV_OK, best = 0, last_chunks = -1;
+  float best_ms = 0.f;
+  for (int zc : {4, 8, 16, 32, 64}) {
+    const int chunks = (g->nz + zc - 1) / zc;
+    if (chunks == last_chunks) continue;  // same launch as the previous candidate
+    last_chunks = chunks;
+    g->tune.pair_zc = zc;
+    st = launch_stencil_pair(g, Gr, sigma, q, V, Y, nvec);
+    if (st == FV_OK) st = cu_ok(cudaEventRecord(e0, g->stream), "cudaEventRecord");
+    for (int r = 0; r < 3 && st == FV_OK; ++r) st = launch_stencil_pair(g, Gr, sigma, q, V, Y, nvec);
+    if (st == FV_OK) st = cu_ok(cudaEventRecord(e1, g->stream), "cudaEventRecord");
+    if (st == FV_OK) st = cu_ok(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    if (st == FV_OK) st = cu_ok(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (st != FV_OK) break;
+    if (best == 0 || ms < best_ms) {
+      best = zc;
+      best_ms = ms;
+    }
+  }
+  g->prof.enabled = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->tune.pair_zc = (st == FV_OK) ? best : 0;
+  g->tune.pair_zc_nvec = (st == FV_OK) ? nvec : 0;
+  return st;
+}
+
+template <typename R>
+static int block_launches(fv_grid_s* g, double Gr, double sigma, const void* q, int nvec, const void* V, void* W) {
+  return jvp_project_block<R>(g, Gr, sigma, (const R*)q, nvec, (const R*)V, (R*)W);
 }
 }
 
-int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
-                         void* W, int use_graph) {
+// one eager pass over every problem (workspace, kernel attributes and tensor-core set-up happen outside any
+// capture), optionally preceded by the autotuner
+static int block_eager(fv_grid_s* g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
+                       void* W, int flags) {
+  if (prec == FV_FP32 && (flags & FV_BATCH_AUTOTUNE))
+    FV_TRY(autotune_pair(g, Gr, sigma, (const float*)q, nvec, (const float*)V));
+  return prec == FV_FP64 ? block_launches<double>(g, Gr, sigma, q, nvec, V, W)
+                         : block_launches<float>(g, Gr, sigma, q, nvec, V, W);
+}
+
+static int check_block(fv_grid_s* g, int prec, const void* q, int nvec, const void* V, const void* W) {
   if (!g || !q || !V || !W) return invalid("null argument");
   if (nvec < 1) return invalid("nvec must be at least 1");
   if (prec != FV_FP64 && prec != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   const size_t bytes = 4 * g->N * (prec == FV_FP64 ? 8 : 4) * (size_t)nvec;
-  const char *v0 = (const char*)V, *w0 = (const char*)W;
-  if ((w0 < v0 + bytes && v0 < w0 + bytes) || (const char*)q == w0) return invalid("W must not overlap V or q");
-  auto launches = [&]() -> int {
-    return prec == FV_FP64 ? batch_launches<double>(g, Gr, sigma, (const double*)q, nvec, (const double*)V, (double*)W)
-                           : batch_launches<float>(g, Gr, sigma, (const float*)q, nvec, (const float*)V, (float*)W);
-  };
-  if (!use_graph) return launches();
-  // first call: workspace, function attributes and tensor-core set-up happen outside the capture
-  if (prec == FV_FP64)
-    FV_TRY(ensure_ws<double>(g));
-  else
-    FV_TRY(ensure_ws<float>(g));
+  const size_t qbytes = 4 * g->N * (prec == FV_FP64 ? 8 : 4);
+  const char *v0 = (const char*)V, *w0 = (const char*)W, *q0 = (const char*)q;
+  if ((w0 < v0 + bytes && v0 < w0 + bytes) || (w0 < q0 + qbytes && q0 < w0 + bytes))
+    return invalid("W must not overlap V or q");
+  return FV_OK;
+}
+
+// launches of one problem's block recorded on `s` (the handle's stream is swapped for the capture)
+static int capture_block(fv_grid_s* g, cudaStream_t s, int prec, double Gr, double sigma, const void* q, int nvec,
+                         const void* V, void* W) {
+  cudaStream_t user = g->stream;
+  const bool prof = g->prof.enabled;
+  g->prof.enabled = false;
+  g->stream = s;
+  const int st = prec == FV_FP64 ? block_launches<double>(g, Gr, sigma, q, nvec, V, W)
+                                 : block_launches<float>(g, Gr, sigma, q, nvec, V, W);
+  g->stream = user;
+  g->prof.enabled = prof;
+  return st;
+}
+
+int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const void* q, int nvec, const void* V,
+                         void* W, int flags) {
+  FV_TRY(check_block(g, prec, q, nvec, V, W));
+  if (!(flags & FV_BATCH_GRAPH)) return block_eager(g, prec, Gr, sigma, q, nvec, V, W, flags);
   fv_grid_s::BatchKey key;
   key.prec = prec;
   key.nvec = nvec;
@@ -787,39 +912,123 @@ int fv_jvp_project_batch(fv_grid g, int prec, double Gr, double sigma, const voi
   key.q = q;
   key.V = V;
   key.W = W;
-  if (!(g->batch_exec && key == g->batch_key)) {
-    if (g->batch_exec) {
-      cudaGraphExecDestroy(g->batch_exec);
-      g->batch_exec = nullptr;
-    }
-    // one eager pass first (kernel attributes are set on first use, which capture does not allow)
-    FV_TRY(launches());
-    if (!g->capture_stream) FV_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
-    FV_CUDA(cudaStreamSynchronize(g->stream));
-    cudaStream_t user = g->stream;
-    const bool prof = g->prof.enabled;
-    g->prof.enabled = false;
-    g->stream = g->capture_stream;
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
-    int st = (e == cudaSuccess) ? launches() : cuda_status(e, "cudaStreamBeginCapture");
-    const cudaError_t e2 = cudaStreamEndCapture(g->capture_stream, &graph);
-    g->stream = user;
-    g->prof.enabled = prof;
-    if (st == FV_OK && e2 != cudaSuccess) st = cuda_status(e2, "cudaStreamEndCapture");
-    if (st == FV_OK) {
-      const cudaError_t e3 = cudaGraphInstantiate(&g->batch_exec, graph, 0);
-      if (e3 != cudaSuccess) st = cuda_status(e3, "cudaGraphInstantiate");
-    }
-    if (graph) cudaGraphDestroy(graph);
-    if (st != FV_OK) {
-      g->batch_exec = nullptr;
-      return st;
-    }
-    g->batch_key = key;
-    return FV_OK;  // the eager pass above already produced W
+  if (g->batch_exec && key == g->batch_key) {
+    FV_CUDA(cudaGraphLaunch(g->batch_exec, g->stream));
+    return FV_OK;
   }
-  FV_CUDA(cudaGraphLaunch(g->batch_exec, g->stream));
+  if (g->batch_exec) {
+    cudaGraphExecDestroy(g->batch_exec);
+    g->batch_exec = nullptr;
+  }
+  // the eager pass produces W for this call; then the same launches are captured for later calls
+  FV_TRY(block_eager(g, prec, Gr, sigma, q, nvec, V, W, flags));
+  if (!g->capture_stream) FV_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
+  int st = (e == cudaSuccess) ? capture_block(g, g->capture_stream, prec, Gr, sigma, q, nvec, V, W)
+                              : cuda_status(e, "cudaStreamBeginCapture");
+  const cudaError_t e2 = cudaStreamEndCapture(g->capture_stream, &graph);
+  if (st == FV_OK && e2 != cudaSuccess) st = cuda_status(e2, "cudaStreamEndCapture");
+  if (st == FV_OK) {
+    const cudaError_t e3 = cudaGraphInstantiate(&g->batch_exec, graph, 0);
+    if (e3 != cudaSuccess) st = cuda_status(e3, "cudaGraphInstantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (st != FV_OK) {
+    g->batch_exec = nullptr;
+    return st;
+  }
+  g->batch_key = key;
+  return FV_OK;
+}
+
+int fv_get_tuning(fv_grid g, int* pair_zchunk, int* tuned_nvec) {
+  if (!g) return invalid("null grid");
+  if (pair_zchunk) *pair_zchunk = g->tune.pair_zc;
+  if (tuned_nvec) *tuned_nvec = g->tune.pair_zc_nvec;
+  return FV_OK;
+}
+
+// ------------------------------------------------------------------ several problems in one graph
+struct fv_batch_plan_s {
+  std::vector<fv_grid_s*> grids;
+  std::vector<unsigned> gens;  // each handle's block-buffer generation at capture
+  cudaGraphExec_t exec = nullptr;
+};
+
+int fv_batch_plan_create(int nprob, const fv_grid* grids, int prec, const double* Gr, const double* sigma,
+                         const void* const* q, const int* nvec, const void* const* V, void* const* W, int flags,
+                         fv_batch_plan* out) {
+  if (!out) return invalid("null output");
+  *out = nullptr;
+  if (nprob < 1 || !grids || !Gr || !sigma || !q || !nvec || !V || !W) return invalid("null argument");
+  for (int i = 0; i < nprob; ++i) {
+    FV_TRY(check_block(grids[i], prec, q[i], nvec[i], V[i], W[i]));
+    for (int j = 0; j < i; ++j)
+      if (grids[j] == grids[i]) return invalid("every problem needs its own grid handle (workspaces run concurrently)");
+  }
+  for (int i = 0; i < nprob; ++i)
+    FV_TRY(block_eager(grids[i], prec, Gr[i], sigma[i], q[i], nvec[i], V[i], W[i], flags));
+  for (int i = 0; i < nprob; ++i) FV_CUDA(cudaStreamSynchronize(grids[i]->stream));
+  // capture: a root stream forks one branch per problem and joins them, so the problems run concurrently
+  std::vector<cudaStream_t> streams(nprob + 1, nullptr);
+  std::vector<cudaEvent_t> events(nprob + 1, nullptr);
+  int st = FV_OK;
+  for (int i = 0; i <= nprob && st == FV_OK; ++i) {
+    st = cu_ok(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    if (st == FV_OK) st = cu_ok(cudaEventCreateWithFlags(&events[i], cudaEventDisableTiming), "cudaEventCreate");
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (st == FV_OK) {
+    cudaStream_t root = streams[nprob];
+    st = cu_ok(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    if (st == FV_OK) {
+      st = cu_ok(cudaEventRecord(events[nprob], root), "cudaEventRecord");
+      for (int i = 0; i < nprob && st == FV_OK; ++i) {
+        st = cu_ok(cudaStreamWaitEvent(streams[i], events[nprob], 0), "cudaStreamWaitEvent");
+        if (st == FV_OK) st = capture_block(grids[i], streams[i], prec, Gr[i], sigma[i], q[i], nvec[i], V[i], W[i]);
+        if (st == FV_OK) st = cu_ok(cudaEventRecord(events[i], streams[i]), "cudaEventRecord");
+        if (st == FV_OK) st = cu_ok(cudaStreamWaitEvent(root, events[i], 0), "cudaStreamWaitEvent");
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+      if (st == FV_OK && e2 != cudaSuccess) st = cuda_status(e2, "cudaStreamEndCapture");
+    }
+  }
+  if (st == FV_OK) st = cu_ok(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+  if (graph) cudaGraphDestroy(graph);
+  for (int i = 0; i <= nprob; ++i) {
+    if (events[i]) cudaEventDestroy(events[i]);
+    if (streams[i]) cudaStreamDestroy(streams[i]);
+  }
+  if (st != FV_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return st;
+  }
+  fv_batch_plan_s* plan = new fv_batch_plan_s();
+  plan->exec = exec;
+  for (int i = 0; i < nprob; ++i) {
+    plan->grids.push_back(grids[i]);
+    plan->gens.push_back(grids[i]->ws.bgen);
+  }
+  *out = plan;
+  return FV_OK;
+}
+
+int fv_batch_plan_launch(fv_batch_plan plan, void* stream) {
+  if (!plan || !plan->exec) return invalid("null plan");
+  for (size_t i = 0; i < plan->grids.size(); ++i)
+    if (plan->grids[i]->ws.bgen != plan->gens[i])
+      return invalid("a grid's block workspace was reallocated after the plan was captured; create the plan again");
+  FV_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+  return FV_OK;
+}
+
+int fv_batch_plan_destroy(fv_batch_plan plan) {
+  if (!plan) return FV_OK;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  delete plan;
   return FV_OK;
 }
 

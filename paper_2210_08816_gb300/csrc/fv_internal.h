@@ -46,6 +46,18 @@ struct Workspace {
   double* partials = nullptr;      // reduction partials
   double* scalars = nullptr;       // device scalars (reduction results)
   double* host_scalars = nullptr;  // pinned host mirror
+  // block of vectors (fv_jvp_project_batch), per precision: J.v outputs (cap * 4N), two transform buffers
+  // (cap * N each), grown on demand
+  void* bY[2] = {nullptr, nullptr};
+  void* bt0[2] = {nullptr, nullptr};
+  void* bt1[2] = {nullptr, nullptr};
+  int bcap[2] = {0, 0};
+  unsigned bgen = 0;  // bumped whenever the block buffers are reallocated (captured graphs refer to them)
+};
+// Launch shapes picked by the autotuner (0 = the built-in default).
+struct Tune {
+  int pair_zc = 0;        // z-planes marched by one CTA of the two-cell J.v stencil
+  int pair_zc_nvec = 0;   // block size the choice was timed on
 };
 
 }  // namespace fv
@@ -92,6 +104,7 @@ struct fv_grid_s {
   double min_width[3];
   mutable fv::Profiler prof;
   fv::TcState tc;
+  fv::Tune tune;
   // batched J.v + projection: the captured launch sequence of the last argument set, replayed while the
   // arguments stay the same, and the private stream it is captured on
   cudaStream_t capture_stream = nullptr;
@@ -146,22 +159,33 @@ template <typename R>
 int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F);
 template <typename R>
 int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);
+// nvec > 1: vel holds nvec states (4N each) and rhs nvec fields (N each), one after another.
 template <typename R>
-int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs);
+int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs, int nvec = 1);
 // out = alpha (Y - G phi) + beta v + gamma w   (velocity; T without G phi).  v, w may be null.
 // norm_slot >= 0: also ||out||^2 into g->ws.scalars[norm_slot] (fused block partials).
 template <typename R>
 int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, const R* v, double beta,
                    const R* w, double gamma, R* out, int norm_slot = -1);
 
+// out_i = (Y_i - G phi_i) + beta v_i for nvec states one after another (Y, v, out: 4N each; phi: N each);
+// v may be null.  No norm.
+template <typename R>
+int launch_correct_block(const fv_grid_s* g, const R* Y, const R* phi, const R* v, double beta, R* out, int nvec);
+
 // FP32 J.v with two x-adjacent cells per thread (kernels_stencil2.cu): nx a multiple of 64, ny >= 16,
 // 16-byte aligned q and v (TMA plane ring).
 bool stencil_pair_eligible(const fv_grid_s* g, const float* q, const float* v);
-int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out);
+// nvec > 1: v and out hold nvec states one after another (4N elements each), all in one launch.
+int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out,
+                        int nvec = 1);
 
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>
 int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp);
+// The same solve for nvec fields stored one after another (N elements each) in rhs, phi and tmp.
+template <typename R>
+int launch_poisson_block(const fv_grid_s* g, const R* rhs, R* phi, R* tmp, int nvec);
 // out = L_f^-1 in for one field f (0..2 velocity with no-slip walls, 3 temperature with Eqs. 4-6 homogeneous
 // and the 1/Pr factor): the diffusion operator of J, inverted by fast diagonalisation (6 passes).
 template <typename R>
@@ -202,7 +226,9 @@ int encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, cons
 // Tensor-core pressure-solve passes (kernels_tc.cu), FP32 only.
 bool tc_eligible(const fv_grid_s* g);
 int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<double>* idc);
-int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale);
+// nvec fields stored one after another are transformed in one launch (persistent form only).
+int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale,
+            int nvec = 1);
 
 // ------------------------------------------------------------------ host linear algebra (host_linalg.cpp)
 // Symmetric tridiagonal eigen-decomposition (implicit QR with Wilkinson shifts).

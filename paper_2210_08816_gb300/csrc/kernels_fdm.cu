@@ -48,6 +48,9 @@ __global__ void __launch_bounds__(256) k_transform(PassArgs t, const R* __restri
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int p0 = blockIdx.x * BM, m0 = blockIdx.y * BN;
+  // blockIdx.z: field of a block of fields stored one after another (P x K in, nm x P out)
+  in += (size_t)blockIdx.z * t.P * t.K;
+  out += (size_t)blockIdx.z * t.nm * t.P;
   R acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -110,7 +113,7 @@ const FdmDev<float>& fdm_of<float>(const fv_grid_s* g) { return g->fdm32; }
 // in[a][b][k] -> out[m][a][b] with M (nm x K); a scaled pass divides by the eigenvalue sums of lam[0..2]
 template <typename R>
 int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale,
-             const R* const lam[3], bool zero_mode, double sfac) {
+             const R* const lam[3], bool zero_mode, double sfac, int nvec = 1) {
   using T = TileCfg<R>;
   PassArgs t{};
   t.P = na * nb;
@@ -120,7 +123,7 @@ int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in,
   t.nb = nb;
   t.zero_mode = zero_mode ? 1 : 0;
   t.sfac = sfac;
-  dim3 grid((t.P + T::BM - 1) / T::BM, (t.nm + T::BN - 1) / T::BN, 1);
+  dim3 grid((t.P + T::BM - 1) / T::BM, (t.nm + T::BN - 1) / T::BN, nvec);
   ProfScope ps(g, PROF_TRANSFORM);
   k_transform<R><<<grid, 256, 0, g->stream>>>(t, in, M, out, lam[0], lam[1], lam[2]);
   FV_CUDA(cudaGetLastError());
@@ -128,9 +131,9 @@ int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in,
 }
 
 template <typename R>
-int pass(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale) {
+int pass(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale, int nvec = 1) {
   const FdmDev<R>& f = fdm_of<R>(g);
-  return pass_ops<R>(g, M, na, nb, K, in, out, scale, f.lam, true, 1.0);
+  return pass_ops<R>(g, M, na, nb, K, in, out, scale, f.lam, true, 1.0, nvec);
 }
 
 template <typename R>
@@ -186,7 +189,37 @@ int launch_poisson<float>(const fv_grid_s* g, const float* rhs, float* phi, floa
   return FV_OK;
 }
 
+template <typename R>
+int launch_poisson_block(const fv_grid_s* g, const R* rhs, R* phi, R* tmp, int nvec) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  if (nvec < 1 || nvec > 65535) {
+    set_error("launch_poisson_block: nvec out of range");
+    return FV_EINVAL;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (g->tc.ready && g->tc.sms > 0) {  // the tensor-core passes over the stacked fields, one launch each
+      FV_TRY(tc_pass(g, 0, false, nz, ny, rhs, tmp, false, nvec));
+      FV_TRY(tc_pass(g, 1, false, nx, nz, tmp, phi, false, nvec));
+      FV_TRY(tc_pass(g, 2, false, ny, nx, phi, tmp, true, nvec));
+      FV_TRY(tc_pass(g, 0, true, nz, ny, tmp, phi, false, nvec));
+      FV_TRY(tc_pass(g, 1, true, nx, nz, phi, tmp, false, nvec));
+      FV_TRY(tc_pass(g, 2, true, ny, nx, tmp, phi, false, nvec));
+      return FV_OK;
+    }
+  }
+  const FdmDev<R>& f = fdm_of<R>(g);
+  FV_TRY(pass<R>(g, f.Einv[0], nz, ny, nx, rhs, tmp, false, nvec));
+  FV_TRY(pass<R>(g, f.Einv[1], nx, nz, ny, tmp, phi, false, nvec));
+  FV_TRY(pass<R>(g, f.Einv[2], ny, nx, nz, phi, tmp, true, nvec));
+  FV_TRY(pass<R>(g, f.E[0], nz, ny, nx, tmp, phi, false, nvec));
+  FV_TRY(pass<R>(g, f.E[1], nx, nz, ny, phi, tmp, false, nvec));
+  FV_TRY(pass<R>(g, f.E[2], ny, nx, nz, tmp, phi, false, nvec));
+  return FV_OK;
+}
+
 template int launch_poisson<double>(const fv_grid_s*, const double*, double*, double*);
+template int launch_poisson_block<double>(const fv_grid_s*, const double*, double*, double*, int);
+template int launch_poisson_block<float>(const fv_grid_s*, const float*, float*, float*, int);
 
 // Diffusion operator of one field, L_f = s_f (L_x (+) L_y (+) L_z), inverted like the pressure operator:
 // velocity component c uses the face-centred Dirichlet operator along its own axis and the cell-centred

@@ -640,13 +640,17 @@ __device__ __forceinline__ float4 ldg4(const float* __restrict__ p, int o) {
 __device__ __forceinline__ float4 ld4(const float* p, int o) { return *reinterpret_cast<const float4*>(p + o); }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
+// blockIdx.z = z-block + nzc * vector (states of 4N, rhs fields of N, one after another)
 __global__ void __launch_bounds__(256) k_divergence4(Geo<float> g, int N, const float* __restrict__ vel,
-                                                      float* __restrict__ rhs) {
+                                                      float* __restrict__ rhs, int nzc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2], pl = nx * ny;
   const int lane = threadIdx.x;
+  const int vec = (int)blockIdx.z / nzc;
+  vel += (size_t)vec * 4 * N;
+  rhs += (size_t)vec * N;
   const int i0 = 4 * (blockIdx.x * 32 + lane);
   const int j = blockIdx.y * 8 + threadIdx.y;
-  const int k0 = blockIdx.z * kVZ, k1 = min(k0 + kVZ, nz);
+  const int k0 = ((int)blockIdx.z - vec * nzc) * kVZ, k1 = min(k0 + kVZ, nz);
   const bool act = i0 < nx && j < ny;
   const float* U = vel;
   const float* V = vel + N;
@@ -692,12 +696,21 @@ __device__ __forceinline__ void acc_sq(float& hi, float& lo, float r) {
 // by the same thread)
 __global__ void __launch_bounds__(256) k_correct4(Geo<float> g, int N, const float* Y, const float* __restrict__ phi,
                                                    float alpha, const float* v, float beta, const float* w,
-                                                   float gamma, float* out, double* __restrict__ part) {
+                                                   float gamma, float* out, double* __restrict__ part, int nzc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2], pl = nx * ny;
   const int lane = threadIdx.x;
+  // blockIdx.z = z-block + nzc * vector (Y, v, w, out: states of 4N; phi: fields of N, one after another)
+  const int vec = (int)blockIdx.z / nzc;
+  if (vec > 0) {
+    Y += (size_t)vec * 4 * N;
+    phi += (size_t)vec * N;
+    if (v) v += (size_t)vec * 4 * N;
+    if (w) w += (size_t)vec * 4 * N;
+    out += (size_t)vec * 4 * N;
+  }
   const int i0 = 4 * (blockIdx.x * 32 + lane);
   const int j = blockIdx.y * 8 + threadIdx.y;
-  const int k0 = blockIdx.z * kVZ, k1 = min(k0 + kVZ, nz);
+  const int k0 = ((int)blockIdx.z - vec * nzc) * kVZ, k1 = min(k0 + kVZ, nz);
   const bool act = i0 < nx && j < ny;
   float4 cx = zero4();
   float cy = 0.f;
@@ -848,19 +861,56 @@ int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R*
 }
 
 template <typename R>
-int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs) {
+int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs, int nvec) {
   dim3 grid, block;
   cell_grid(g, grid, block);
   ProfScope ps(g, PROF_DIVERGENCE);
   if constexpr (sizeof(R) == 4) {
     if (quad_ok(g, {vel, rhs})) {
-      k_divergence4<<<quad_grid(g), dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, vel, rhs);
+      dim3 qg = quad_grid(g);
+      const int nzc = (int)qg.z;
+      if ((long long)nzc * nvec > 65535) {
+        set_error("launch_divergence: too many vectors in one block");
+        return FV_EINVAL;
+      }
+      qg.z = nzc * nvec;
+      k_divergence4<<<qg, dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, vel, rhs, nzc);
       FV_CUDA(cudaGetLastError());
       return FV_OK;
     }
   }
-  k_divergence<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, vel, rhs);
-  FV_CUDA(cudaGetLastError());
+  for (int i = 0; i < nvec; ++i) {
+    k_divergence<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, vel + (size_t)i * 4 * g->N,
+                                                   rhs + (size_t)i * g->N);
+    FV_CUDA(cudaGetLastError());
+  }
+  return FV_OK;
+}
+
+template <typename R>
+int launch_correct_block(const fv_grid_s* g, const R* Y, const R* phi, const R* v, double beta, R* out, int nvec) {
+  bool quad = false;
+  if constexpr (sizeof(R) == 4) quad = quad_ok(g, {Y, phi, v, out});
+  if (!quad) {
+    for (int i = 0; i < nvec; ++i)
+      FV_TRY(launch_correct<R>(g, Y + (size_t)i * 4 * g->N, phi + (size_t)i * g->N, 1.0,
+                               v ? v + (size_t)i * 4 * g->N : nullptr, beta, nullptr, 0.0,
+                               out + (size_t)i * 4 * g->N, -1));
+    return FV_OK;
+  }
+  if constexpr (sizeof(R) == 4) {
+    dim3 qg = quad_grid(g);
+    const int nzc = (int)qg.z;
+    if ((long long)nzc * nvec > 65535) {
+      set_error("launch_correct_block: too many vectors in one block");
+      return FV_EINVAL;
+    }
+    qg.z = nzc * nvec;
+    ProfScope ps(g, PROF_CORRECT);
+    k_correct4<<<qg, dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, Y, phi, 1.0f, v, (float)beta, nullptr, 0.0f,
+                                                  out, nullptr, nzc);
+    FV_CUDA(cudaGetLastError());
+  }
   return FV_OK;
 }
 
@@ -879,7 +929,8 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
     if constexpr (sizeof(R) == 4) {
       if (quad)
         k_correct4<<<grid, dim3(32, 8), 0, g->stream>>>(g->geo32, (int)g->N, Y, phi, (float)alpha, v, (float)beta, w,
-                                                        (float)gamma, out, want ? g->ws.partials : nullptr);
+                                                        (float)gamma, out, want ? g->ws.partials : nullptr,
+                                                        (int)grid.z);
     }
     if (!quad)
       k_correct<R><<<grid, block, 0, g->stream>>>(geo_of<R>(g), (int)g->N, Y, phi, (R)alpha, v, (R)beta, w,
@@ -894,8 +945,12 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
 template int launch_residual<double>(const fv_grid_s*, double, const double*, double*);
 template int launch_jvp<double>(const fv_grid_s*, double, double, const double*, const double*, double*);
 template int launch_jvp<float>(const fv_grid_s*, double, double, const float*, const float*, float*);
-template int launch_divergence<double>(const fv_grid_s*, const double*, double*);
-template int launch_divergence<float>(const fv_grid_s*, const float*, float*);
+template int launch_divergence<double>(const fv_grid_s*, const double*, double*, int);
+template int launch_divergence<float>(const fv_grid_s*, const float*, float*, int);
+template int launch_correct_block<double>(const fv_grid_s*, const double*, const double*, const double*, double,
+                                          double*, int);
+template int launch_correct_block<float>(const fv_grid_s*, const float*, const float*, const float*, double, float*,
+                                         int);
 template int launch_correct<double>(const fv_grid_s*, const double*, const double*, double, const double*, double,
                                     const double*, double, double*, int);
 template int launch_correct<float>(const fv_grid_s*, const float*, const float*, double, const float*, double,

@@ -20,7 +20,7 @@ constexpr int kPX = 64, kPY = 8, kPHY = kPY + 2;
 constexpr int kPW2 = 72;            // ring row: x from i0 - 4 to i0 + 67 (TMA x start on a 16-byte boundary)
 constexpr int kPX0 = 4;             // column of the tile's first cell
 constexpr int kPL2 = kPHY * kPW2;   // one array's plane tile
-constexpr int kPZChunk = 32, kPRing = 4, kPNA = 8;
+constexpr int kPZChunk = 32, kPRing = 4, kPNA = 8;  // default z-chunk (planes marched by one CTA)
 constexpr long long kPWaitLimit = 1LL << 22;
 
 // ---------------------------------------------------------------- pair arithmetic
@@ -234,18 +234,25 @@ __device__ __forceinline__ bool bar_wait2(uint32_t bar, uint32_t parity, int* er
 
 
 // J.v, FP32, two cells per thread; ring planes arrive as one 4D TMA box per state (x, y, z, field)
+template <bool BLOCK>
 __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
     k_stencil_pair(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int* err,
-                   Geo<float> g, int N, float Gr, float invPr, float sigma, float* __restrict__ out) {
+                   Geo<float> g, int N, float Gr, float invPr, float sigma, float* __restrict__ out, int zc,
+                   int nch) {
   constexpr uint32_t kBox = 4u * kPL2 * sizeof(float);  // one state's box: 4 fields x kPHY x kPW2
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[kPRing];
   float* sm = reinterpret_cast<float*>(smem_raw);  // [kPRing][kPNA][kPL2]
   const int tid = threadIdx.x;
   const int tx = tid % (kPX / 2), ty = tid / (kPX / 2);
-  const int i0 = blockIdx.x * kPX, j0 = blockIdx.y * kPY, k0 = blockIdx.z * kPZChunk;
+  // BLOCK: blockIdx.z = z-chunk + nch * vector, vector `vec` of the block is fields 4 vec .. 4 vec + 3 of
+  // tmv; otherwise one vector in chunks of kPZChunk planes
+  if (!BLOCK) zc = kPZChunk, nch = gridDim.z;
+  const int vec = BLOCK ? (int)blockIdx.z / nch : 0;
+  const int i0 = blockIdx.x * kPX, j0 = blockIdx.y * kPY, k0 = ((int)blockIdx.z - vec * nch) * zc;
+  if (BLOCK) out += (size_t)vec * 4 * N;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int kend = min(k0 + kPZChunk, nz);
+  const int kend = min(k0 + zc, nz);
   if (tid == 0) {
     for (int s2 = 0; s2 < kPRing; ++s2)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr2(&bar[s2])) : "memory");
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
             "%5, %6}], [%2];" ::"r"(smem_addr2(slot + 4 * kPL2)),
-            "l"(reinterpret_cast<uint64_t>(&tmv)), "r"(b), "r"(i0 - kPX0), "r"(j0 - 1), "r"(kk), "r"(0)
+            "l"(reinterpret_cast<uint64_t>(&tmv)), "r"(b), "r"(i0 - kPX0), "r"(j0 - 1), "r"(kk), "r"(4 * vec)
             : "memory");
       }
     } else {  // a plane outside the domain: zeros, and a plain arrival completes the barrier phase
@@ -322,9 +329,10 @@ __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
   }
 }
 
-// 4D tensor map of one FP32 state (x, y, z, field) with boxes of kPW2 x kPHY x 1 x 4 elements
-int pair_map(const fv_grid_s* g, const float* ptr, CUtensorMap* m) {
-  const uint64_t dims[4] = {(uint64_t)g->nx, (uint64_t)g->ny, (uint64_t)g->nz, 4};
+// 4D tensor map of nvec FP32 states stored one after another (x, y, z, field; 4 nvec fields) with boxes
+// of kPW2 x kPHY x 1 x 4 elements
+int pair_map(const fv_grid_s* g, const float* ptr, CUtensorMap* m, int nvec = 1) {
+  const uint64_t dims[4] = {(uint64_t)g->nx, (uint64_t)g->ny, (uint64_t)g->nz, 4 * (uint64_t)nvec};
   const uint64_t strides[3] = {g->nx * sizeof(float), (uint64_t)g->nx * g->ny * sizeof(float), g->N * sizeof(float)};
   const uint32_t box[4] = {(uint32_t)kPW2, (uint32_t)kPHY, 1, 4};
   return encode_tensor_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ptr, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -336,22 +344,35 @@ bool stencil_pair_eligible(const fv_grid_s* g, const float* q, const float* v) {
   return g->nx % kPX == 0 && g->ny >= 16 && ((uintptr_t)q % 16) == 0 && ((uintptr_t)v % 16) == 0;
 }
 
-int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out) {
+int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out,
+                        int nvec) {
   const size_t smem = (size_t)kPRing * kPNA * kPL2 * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
-    FV_CUDA(cudaFuncSetAttribute(k_stencil_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FV_CUDA(cudaFuncSetAttribute(k_stencil_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FV_CUDA(cudaFuncSetAttribute(k_stencil_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
+  }
+  // blocks of vectors march the z-chunk the autotuner picked (if it ran); single vectors the default
+  const int zc = (nvec > 1 && g->tune.pair_zc > 0) ? g->tune.pair_zc : kPZChunk;
+  const int nch = (g->nz + zc - 1) / zc;
+  if (nvec < 1 || (long long)nch * nvec > 65535) {
+    set_error("launch_stencil_pair: too many vectors in one block for this z-chunk");
+    return FV_EINVAL;
   }
   CUtensorMap tq, tv;
   std::memset(&tq, 0, sizeof(tq));
   std::memset(&tv, 0, sizeof(tv));
   FV_TRY(pair_map(g, q, &tq));
-  FV_TRY(pair_map(g, v, &tv));
-  dim3 grid(g->nx / kPX, (g->ny + kPY - 1) / kPY, (g->nz + kPZChunk - 1) / kPZChunk);
+  FV_TRY(pair_map(g, v, &tv, nvec));
+  dim3 grid(g->nx / kPX, (g->ny + kPY - 1) / kPY, nch * nvec);
   ProfScope ps(g, PROF_STENCIL);
-  k_stencil_pair<<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, g->geo32, (int)g->N, (float)Gr,
-                                                           (float)(1.0 / g->Pr), (float)sigma, out);
+  if (nvec > 1)
+    k_stencil_pair<true><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, g->geo32, (int)g->N, (float)Gr,
+                                                                 (float)(1.0 / g->Pr), (float)sigma, out, zc, nch);
+  else
+    k_stencil_pair<false><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, g->geo32, (int)g->N, (float)Gr,
+                                                                  (float)(1.0 / g->Pr), (float)sigma, out, zc, nch);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

@@ -356,7 +356,7 @@ template <bool SCALE, bool BWD>
 __global__ void __launch_bounds__(kTcpThreads, 1)
     k_transform_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB1hi,
                     const __grid_constant__ CUtensorMap tmB1lo, const __grid_constant__ CUtensorMap tmB2hi,
-                    const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int n,
+                    const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int Ptot, int n,
                     const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
                     int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
   const uint32_t stage_bytes = 4u * kTcABytes + 4u * b_bytes;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nst = n / (2 * kTcBK);
-  const int ntiles = (P + kTcBM - 1) / kTcBM;
+  const int ntiles = (Ptot + kTcBM - 1) / kTcBM;
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
   if (threadIdx.x == 0) {
@@ -534,10 +534,14 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       const bool ok = mbar_wait(smem_u32(&bar_accf[b]), (ti / 2) & 1, err, 18);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int p = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM + row;
+      // row pg of the stacked block: row p of field vec (fields of P x n, one after another)
+      const int pg = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM + row;
+      const int vec = pg / P, p = pg - vec * P;
+      const bool live = pg < Ptot;
+      float* __restrict__ o = out + (long long)vec * P * n;
       float sa = 0.f, sb2 = 0.f;
       int pa = 0, pb = 0;
-      if (SCALE && p < P) {
+      if (SCALE && live) {
         pa = p / nb;
         pb = p - pa * nb;
         sa = ly[pa];
@@ -548,21 +552,21 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         uint32_t r1[16], r2[16];
         tmem_ld16(lane_base + (uint32_t)c0, r1);
         tmem_ld16(lane_base + (uint32_t)(h + c0), r2);
-        if (p < P) {
+        if (live) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int m = c0 + jj;
             const float v1 = __uint_as_float(r1[jj]), v2 = __uint_as_float(r2[jj]);
             if (BWD) {  // cells m and n-1-m
-              out[(long long)m * P + p] = v1 + v2;
-              out[(long long)(n - 1 - m) * P + p] = v1 - v2;
+              o[(long long)m * P + p] = v1 + v2;
+              o[(long long)(n - 1 - m) * P + p] = v1 - v2;
             } else if (SCALE) {  // symmetric mode m, antisymmetric mode h + m
               const float s1 = (m == 0 && pa == 0 && pb == 0) ? 0.f : v1 * rcp_approx(lz_s[m] + sa + sb2);
-              out[(long long)m * P + p] = s1;
-              out[(long long)(h + m) * P + p] = v2 * rcp_approx(lz_s[h + m] + sa + sb2);
+              o[(long long)m * P + p] = s1;
+              o[(long long)(h + m) * P + p] = v2 * rcp_approx(lz_s[h + m] + sa + sb2);
             } else {
-              out[(long long)m * P + p] = v1;
-              out[(long long)(h + m) * P + p] = v2;
+              o[(long long)m * P + p] = v1;
+              o[(long long)(h + m) * P + p] = v2;
             }
           }
         }
@@ -767,13 +771,21 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<dou
 }
 
 // one pass: in[a][b][k] (na*nb rows of n) -> out[m][a][b] with the matrices of `axis`; bwd selects the
-// backward (modes -> cells) matrices.  Mode indices are in the tensor-core order throughout.
-int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale) {
+// backward (modes -> cells) matrices.  Mode indices are in the tensor-core order throughout.  nvec > 1:
+// that many fields of na*nb*n elements one after another in `in` and in `out`, each transformed alone,
+// all in one persistent launch.
+int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float* in, float* out, bool scale,
+            int nvec) {
   const int n = (axis == 0) ? g->nx : (axis == 1) ? g->ny : g->nz;
   const long long P = (long long)na * nb;
+  if (nvec < 1 || (nvec > 1 && !(kTcPersistent && g->tc.sms > 0)) || P * nvec > (1LL << 30)) {
+    set_error("tc_pass: batch of fields not supported here");
+    return FV_EINVAL;
+  }
+  const long long Ptot = P * nvec;
   CUtensorMap tmA;
-  FV_TRY(encode(&tmA, in, P, n, kTcBM));
-  const long long ntiles = (P + kTcBM - 1) / kTcBM;
+  FV_TRY(encode(&tmA, in, Ptot, n, kTcBM));
+  const long long ntiles = (Ptot + kTcBM - 1) / kTcBM;
   const dim3 grid((unsigned)ntiles);
   const size_t smem = tc_smem_bytes(n);
   const CUtensorMap* B = g->tc.B[axis] + (bwd ? 4 : 0);
@@ -781,14 +793,15 @@ int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float*
   if (kTcPersistent && g->tc.sms > 0) {
     const dim3 pgrid((unsigned)std::min<long long>(ntiles, g->tc.sms));
     if (bwd)
-      k_transform_tcp<false, true><<<pgrid, kTcpThreads, smem, g->stream>>>(tmA, B[0], B[1], B[2], B[3], out, (int)P,
-                                                                          n, nullptr, nullptr, nullptr, nb, g->ws.err);
+      k_transform_tcp<false, true><<<pgrid, kTcpThreads, smem, g->stream>>>(
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err);
     else if (scale)
       k_transform_tcp<true, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb, g->ws.err);
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb,
+          g->ws.err);
     else
       k_transform_tcp<false, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, n, nullptr, nullptr, nullptr, nb, g->ws.err);
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err);
     FV_CUDA(cudaGetLastError());
     return FV_OK;
   }

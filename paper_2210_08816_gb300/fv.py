@@ -84,6 +84,11 @@ def lib():
             "fv_convert": (i, [vp, i, vp, vp]),
             "fv_diffusion_solve": (i, [vp, i, vp, vp]),
             "fv_jvp_project_batch": (i, [vp, i, d, d, vp, i, vp, vp, i]),
+            "fv_get_tuning": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+            "fv_batch_plan_create": (i, [i, C.POINTER(vp), i, C.POINTER(d), C.POINTER(d), C.POINTER(vp),
+                                         C.POINTER(i), C.POINTER(vp), C.POINTER(vp), i, C.POINTER(vp)]),
+            "fv_batch_plan_launch": (i, [vp, vp]),
+            "fv_batch_plan_destroy": (i, [vp]),
             "fv_newton_default_opts": (None, [C.POINTER(fv_newton_opts)]),
             "newton_steady": (i, [vp, d, vp, C.POINTER(fv_newton_opts), C.POINTER(fv_newton_report)]),
             "fv_arnoldi_default_opts": (None, [C.POINTER(fv_arnoldi_opts)]),
@@ -104,6 +109,7 @@ def lib():
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
             "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
+            "fv_get_tuning", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
             "fv_newton_default_opts",
             "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
             "fv_strerror", "fv_last_error"]
@@ -201,13 +207,67 @@ def fv_project(g: Grid, prec, v, max_it=1, tol=0.0, want_div=False):
     return it.value, (dv.value if want_div else None)
 
 
-def fv_jvp_project_batch(g: Grid, prec, Gr, sigma, q, V, W, nvec, use_graph=False):
+FV_BATCH_GRAPH = 1
+FV_BATCH_AUTOTUNE = 2
+
+
+def fv_jvp_project_batch(g: Grid, prec, Gr, sigma, q, V, W, nvec, use_graph=False, autotune=False):
     """W_i = P (J V_i - sigma V_i) + sigma V_i for nvec vectors stored back to back in V and W."""
     dt = g.dtype(prec)
+    flags = (FV_BATCH_GRAPH if use_graph else 0) | (FV_BATCH_AUTOTUNE if autotune else 0)
     _check(lib().fv_jvp_project_batch(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"), int(nvec),
-                                      _ptr(V, dt, g.n * nvec, "V"), _ptr(W, dt, g.n * nvec, "W"),
-                                      1 if use_graph else 0), "fv_jvp_project_batch")
+                                      _ptr(V, dt, g.n * nvec, "V"), _ptr(W, dt, g.n * nvec, "W"), flags),
+           "fv_jvp_project_batch")
     return W
+
+
+def fv_get_tuning(g: Grid):
+    """(z-chunk of the block stencil picked by the autotuner (0 = default), block size it was timed on)."""
+    zc, nv = C.c_int(0), C.c_int(0)
+    _check(lib().fv_get_tuning(g.h, C.byref(zc), C.byref(nv)), "fv_get_tuning")
+    return zc.value, nv.value
+
+
+class BatchPlan:
+    """Several problems (grid handle, Gr, sigma, q, block V -> W) captured into one CUDA graph whose branches
+    run concurrently (fv_batch_plan_create); launch() replays it on a stream.  Keeps references to the
+    tensors and grids so that they outlive the plan."""
+
+    def __init__(self, problems, prec, autotune=False):
+        n = len(problems)
+        dt = None
+        hs, grs, sig, qs, nv, vs, ws = [], [], [], [], [], [], []
+        for (g, Gr, sigma, q, V, W, nvec) in problems:
+            dt = g.dtype(prec)
+            hs.append(g.h)
+            grs.append(float(Gr))
+            sig.append(float(sigma))
+            qs.append(_ptr(q, dt, g.n, "q"))
+            vs.append(_ptr(V, dt, g.n * nvec, "V"))
+            ws.append(_ptr(W, dt, g.n * nvec, "W"))
+            nv.append(int(nvec))
+        self._keep = problems
+        arr = lambda t, xs: (t * n)(*xs)
+        h = C.c_void_p()
+        _check(lib().fv_batch_plan_create(n, arr(C.c_void_p, hs), prec, arr(C.c_double, grs), arr(C.c_double, sig),
+                                          arr(C.c_void_p, qs), arr(C.c_int, nv), arr(C.c_void_p, vs),
+                                          arr(C.c_void_p, ws), FV_BATCH_AUTOTUNE if autotune else 0, C.byref(h)),
+               "fv_batch_plan_create")
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(lib().fv_batch_plan_launch(self.h, C.c_void_p(stream)), "fv_batch_plan_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fv_batch_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fv_diffusion_solve(g: Grid, prec, x, out):

@@ -290,3 +290,87 @@ def test_batched_fused_path_eager_and_graph(fv, prec_name, shape):
     ref2 = torch.empty_like(V[:g.n])
     fv.fv_jvp_project(g, prec, 2 * Gr, sigma, q, V[:g.n], ref2)
     assert torch.equal(W[:g.n], ref2)
+
+
+def test_block_path_tensorcore_autotuned(fv):
+    """A block of FP32 vectors on a grid where every stage has its block form (two-cell stencil, quad
+    divergence and correction, tcgen05 passes over the stacked fields), with the z-chunk autotuner on:
+    the per-vector results of fv_jvp_project to FP32 round-off (each cell's arithmetic is the same; only
+    the grouping of cells into CTAs and tiles differs), and the oracle within the fused-path bound."""
+    shape = (64, 64, 64)
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    nvec, Gr, sigma = 6, 1.0e5, -750.0
+    q = dev(state(og, 41), torch.float32)
+    vs = [round32(vector(og, 50 + i)) for i in range(nvec)]
+    V = torch.cat([dev(v, torch.float32) for v in vs])
+    ref = torch.empty_like(V)
+    for i in range(nvec):
+        fv.fv_jvp_project(g, fv.FV_FP32, Gr, sigma, q, V[i * g.n:(i + 1) * g.n], ref[i * g.n:(i + 1) * g.n])
+    W = torch.empty_like(V)
+    for graph in (False, True, True):
+        W.zero_()
+        fv.fv_jvp_project_batch(g, fv.FV_FP32, Gr, sigma, q, V, W, nvec, use_graph=graph, autotune=True)
+        torch.cuda.synchronize()
+        for i in range(nvec):
+            a, b = W[i * g.n:(i + 1) * g.n], ref[i * g.n:(i + 1) * g.n]
+            assert float((a - b).abs().max()) <= 1e-6 * float(b.abs().max()), (graph, i)
+    zc, nv = fv.fv_get_tuning(g)
+    assert zc in (4, 8, 16, 32, 64) and nv == nvec
+    # one vector of the block against the oracle (FP32-rounded inputs, FP64 oracle)
+    qa = round32(state(og, 41))
+    P = Projector(og)
+    i = 3
+    qf, vf = D.from_api(og, qa), D.from_api(og, vs[i])
+    J = D.jvp_full(og, Gr, qf, vf)
+    r = P.full([J[c] - sigma * vf[c] for c in range(4)])
+    exp = D.to_api(og, [r[c] + sigma * vf[c] for c in range(4)])
+    assert rel(host(W[i * g.n:(i + 1) * g.n], og.shape), exp) <= TOL32_PROJ
+    g.close()
+
+
+def test_batch_plan_several_grids_one_graph(fv):
+    """fv_batch_plan: three continuation points on grids of different sizes (one of them without the
+    block stencil) in one captured graph with concurrent branches give the per-vector results; a replay
+    reads the vectors' current contents; growing a handle's block buffers invalidates the plan."""
+    probs = [((64, 64, 64), 3.0e7, 3), ((40, 36, 32), 7.4e7, 2), ((96, 32, 48), 2.5e8, 2)]
+    keep = []
+    for k, (shape, Gr, nvec) in enumerate(probs):
+        og = D.Grid(*shape, stretch=1.5, Pr=PR)
+        g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+        q = dev(state(og, 60 + k), torch.float32)
+        V = torch.cat([dev(vector(og, 70 + 10 * k + i), torch.float32) for i in range(nvec)])
+        W = torch.empty_like(V)
+        sigma = -100.0 * (k + 1)
+        ref = torch.empty_like(V)
+        for i in range(nvec):
+            fv.fv_jvp_project(g, fv.FV_FP32, Gr, sigma, q, V[i * g.n:(i + 1) * g.n], ref[i * g.n:(i + 1) * g.n])
+        keep.append((g, Gr, sigma, q, V, W, nvec, ref))
+    plan = fv.BatchPlan([k[:7] for k in keep], fv.FV_FP32, autotune=True)
+
+    def check(scale):
+        torch.cuda.synchronize()
+        for (g, Gr, sigma, q, V, W, nvec, ref) in keep:
+            err = float((W - scale * ref).abs().max())
+            assert err <= 1e-5 * float(ref.abs().max()) * scale, (g.shape, err)
+
+    check(1.0)
+    for (_, _, _, _, _, W, _, _) in keep:
+        W.zero_()
+    plan.launch(torch.cuda.current_stream().cuda_stream)
+    check(1.0)
+    for (_, _, _, _, V, W, _, _) in keep:
+        V.mul_(2.0)
+        W.zero_()
+    plan.launch(torch.cuda.current_stream().cuda_stream)
+    check(2.0)
+    # a larger block on the first handle reallocates its block buffers: the plan refuses to replay
+    g0, Gr0, s0, q0 = keep[0][:4]
+    V2 = torch.cat([keep[0][4]] * 2)
+    W2 = torch.empty_like(V2)
+    fv.fv_jvp_project_batch(g0, fv.FV_FP32, Gr0, s0, q0, V2, W2, 2 * keep[0][6])
+    with pytest.raises(fv.FvError):
+        plan.launch(torch.cuda.current_stream().cuda_stream)
+    plan.close()
+    for k in keep:
+        k[0].close()
