@@ -230,6 +230,13 @@ typedef struct {
                              grid is refined; 0: none */
     int forcing;          /* 1 (default): inner tolerance by Eisenstat-Walker, 0.9 (r_k/r_{k-1})^2
                              within [max(krylov_tol, target / (2 r_k)), 1e-2]; 0: krylov_tol */
+    double ptc_dt0;       /* > 0: pseudo-transient continuation with this first pseudo-time step:
+                             step k solves (P J - I/dt_k) delta = -P F (preconditioner
+                             P (L - I/dt_k)^-1); dt grows by (r_{k-1}/r_k)^2 clipped to [1.5, 10]
+                             after a step that lowered ||P F|| and halves (not below ptc_dt0) after
+                             one that did not; plain Newton once dt_k > 1e4.  A globalisation for high Gr,
+                             where the steady state is stable but far from the continuation's
+                             previous point; it does not change the converged state.  0 (default): off */
 } fv_newton_opts;
 
 typedef struct {

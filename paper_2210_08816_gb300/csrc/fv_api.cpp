@@ -386,24 +386,27 @@ struct Vec {
 // out = L^-1 in, field by field (the diffusion operator of J with homogeneous wall data); in and out
 // may alias.
 template <typename R>
-static int diffusion_solve(fv_grid_s* g, const R* in, R* out) {
+static int diffusion_solve(fv_grid_s* g, const R* in, R* out, double s = 0.0) {
   FV_TRY(ensure_ws<R>(g));
   R* tmp = (R*)g->ws.t0[prec_index<R>()];
-  for (int f = 0; f < 4; ++f) FV_TRY(launch_field_solve<R>(g, f, in + (size_t)f * g->N, out + (size_t)f * g->N, tmp));
+  for (int f = 0; f < 4; ++f)
+    FV_TRY(launch_field_solve<R>(g, f, in + (size_t)f * g->N, out + (size_t)f * g->N, tmp, s));
   return FV_OK;
 }
 
 // Right preconditioner M^-1 = P L^-1 (the diffusion part of J inverted, then projected): it removes
 // the stiff diffusion eigenvalues (up to ~12 / h_min^2) from P J M^-1, but P and L do not commute at
 // no-slip walls, so P J M^-1 is not a compact perturbation of P there.
+// With a pseudo-time shift s: M^-1 = P (L - s I)^-1 for the operator P J - s I.
 template <typename R>
-static int apply_precond(fv_grid_s* g, const R* in, R* out) {
-  FV_TRY(diffusion_solve<R>(g, in, out));
+static int apply_precond(fv_grid_s* g, const R* in, R* out, double s = 0.0) {
+  FV_TRY(diffusion_solve<R>(g, in, out, s));
   return project_inplace<R>(g, out, 1, 0.0, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ BiCGstab(2) and GMRES
-// y = A x = P (J - sigma) x + sigma x, or A M^-1 x when `pre` (a 4N scratch vector) is set.
+// y = A x = P (J - sigma) x + sigma x - s x, or A M^-1 x when `pre` (a 4N scratch vector) is set; s is the
+// reciprocal pseudo-time step (0: the Newton operator itself).
 template <typename R>
 struct Operator {
   fv_grid_s* g;
@@ -411,13 +414,18 @@ struct Operator {
   const R* q;
   long long* matvecs;
   R* pre = nullptr;
+  double s = 0.0;
   int apply(const R* x, R* y) {
     ++*matvecs;
+    const R* in = x;
     if (pre) {
-      FV_TRY(apply_precond<R>(g, x, pre));
-      return jvp_project<R>(g, Gr, sigma, q, pre, y);
+      FV_TRY(apply_precond<R>(g, x, pre, s));
+      in = pre;
     }
-    return jvp_project<R>(g, Gr, sigma, q, x, y);
+    FV_TRY(jvp_project<R>(g, Gr, sigma, q, in, y));
+    if (s == 0.0) return FV_OK;
+    Vec<R> V{g, 4 * g->N};
+    return V.lin(y, {{1.0, y}, {-s, in}});
   }
 };
 
@@ -1122,6 +1130,7 @@ void fv_newton_default_opts(fv_newton_opts* o) {
   o->gr_ratio = 2.0;
   o->precond = 1;
   o->forcing = 1;
+  o->ptc_dt0 = 0.0;
 }
 
 void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
@@ -1168,6 +1177,11 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
   // the FP64 outer loop refines past either
   const double ktol = mixed ? std::max(o.krylov_tol, o.precond ? 1e-3 : 1e-5) : o.krylov_tol;
   double r0 = -1.0, r_prev = -1.0, eta_prev = 1e-2;
+  // pseudo-transient continuation: step k solves (P J - I / dt_k) delta = -P F; after a step that lowered
+  // the residual dt grows by (r_{k-1} / r_k)^2 clipped to [1.5, 10] (switched evolution relaxation with a
+  // floor on the growth), after one that did not it halves (never below dt_0); plain Newton once
+  // dt > 1e4 (|lambda| dt ~ 1e6 for the slowest modes of this problem)
+  double dt = o.ptc_dt0;
   int steps = 0;
   DevBuf<double> qt;
   FV_TRY(qt.alloc(n));
@@ -1224,6 +1238,12 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
     long long mv = 0;
     Operator<R> A{g, Gr, sigma, qop, &mv};
     A.pre = o.precond ? pre.p : nullptr;
+    if (dt > 0.0) {
+      if (r_prev > 0.0)
+        dt = (rn < r_prev) ? dt * std::min(10.0, std::max(1.5, (r_prev / rn) * (r_prev / rn)))
+                           : std::max(o.ptc_dt0, 0.5 * dt);
+      A.s = (dt < 1e4) ? 1.0 / dt : 0.0;
+    }
     SolveInfo info;
     // inner tolerance: fixed krylov_tol, or Eisenstat-Walker (choice 2): eta = 0.9 (r_k / r_{k-1})^2,
     // at most 1e-2 (safeguard max(eta, 0.9 eta_{k-1}^2)), at least krylov_tol and half of what takes the
@@ -1237,6 +1257,7 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
     }
     eta_prev = eta;
     r_prev = rn;
+    if (A.s != 0.0) eta = std::max(eta, 1e-3);  // a pseudo-time step needs no accurate solve
     FV_TRY(bicgstab2<R>(A, b, x.p, eta, o.max_matvec, work.p, info));
     if (info.status != FV_OK && (info.breakdown || info.stalled)) {
       SolveInfo info2;
@@ -1245,7 +1266,7 @@ static int newton_at(fv_grid_s* g, double Gr, double* q, const fv_newton_opts& o
     }
     rep->matvecs += (int)mv;
     if (o.precond) {  // right preconditioning: delta = M^-1 y
-      FV_TRY(apply_precond<R>(g, x.p, pre.p));
+      FV_TRY(apply_precond<R>(g, x.p, pre.p, A.s));
       Vec<R> VP{g, n};
       FV_TRY(VP.copy(x.p, pre.p));
     }
@@ -1287,7 +1308,7 @@ extern "C" int newton_steady(fv_grid g, double Gr, double* q_inout, const fv_new
     fv_newton_default_opts(&o);
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   if (o.max_newton < 0 || o.max_matvec < 4 || o.gmres_m < 1 || o.gmres_m > 200 || o.precond < 0 || o.precond > 1 ||
-      o.forcing < 0 || o.forcing > 1)
+      o.forcing < 0 || o.forcing > 1 || !(o.ptc_dt0 >= 0.0))
     return invalid("bad Newton options");
   fv_newton_report rep;
   std::memset(&rep, 0, sizeof(rep));

@@ -188,8 +188,9 @@ template <typename R>
 int launch_poisson_block(const fv_grid_s* g, const R* rhs, R* phi, R* tmp, int nvec);
 // out = L_f^-1 in for one field f (0..2 velocity with no-slip walls, 3 temperature with Eqs. 4-6 homogeneous
 // and the 1/Pr factor): the diffusion operator of J, inverted by fast diagonalisation (6 passes).
+// s != 0: (L_f - s I)^-1 (the shifted operator of a pseudo-time step 1/s).
 template <typename R>
-int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp);
+int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp, double s = 0.0);
 
 // BLAS-1 and reductions (kernels_blas.cu).  Results land in g->ws.scalars[slot...].
 template <typename R>

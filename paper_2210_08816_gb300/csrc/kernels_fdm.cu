@@ -35,6 +35,7 @@ struct PassArgs {
   int nb;
   int zero_mode;         // the (0,0,0) mode is the null space (Neumann): set it to zero
   double sfac;
+  double shift;          // scaled pass: sfac / (lam_z + lam_y + lam_x - shift)
 };
 
 template <typename R>
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256) k_transform(PassArgs t, const R* __restri
       R val = acc[i][j];
       if (t.scale) {
         const int a = p / t.nb, b = p - a * t.nb;
-        val = (t.zero_mode && m == 0 && a == 0 && b == 0) ? R(0) : R(t.sfac) * val / (lz[m] + ly[a] + lx[b]);
+        val = (t.zero_mode && m == 0 && a == 0 && b == 0) ? R(0) : R(t.sfac) * val / (lz[m] + ly[a] + lx[b] - R(t.shift));
       }
       out[(long long)m * t.P + p] = val;
     }
@@ -113,7 +114,7 @@ const FdmDev<float>& fdm_of<float>(const fv_grid_s* g) { return g->fdm32; }
 // in[a][b][k] -> out[m][a][b] with M (nm x K); a scaled pass divides by the eigenvalue sums of lam[0..2]
 template <typename R>
 int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in, R* out, bool scale,
-             const R* const lam[3], bool zero_mode, double sfac, int nvec = 1) {
+             const R* const lam[3], bool zero_mode, double sfac, int nvec = 1, double shift = 0.0) {
   using T = TileCfg<R>;
   PassArgs t{};
   t.P = na * nb;
@@ -123,6 +124,7 @@ int pass_ops(const fv_grid_s* g, const R* M, int na, int nb, int K, const R* in,
   t.nb = nb;
   t.zero_mode = zero_mode ? 1 : 0;
   t.sfac = sfac;
+  t.shift = shift;
   dim3 grid((t.P + T::BM - 1) / T::BM, (t.nm + T::BN - 1) / T::BN, nvec);
   ProfScope ps(g, PROF_TRANSFORM);
   k_transform<R><<<grid, 256, 0, g->stream>>>(t, in, M, out, lam[0], lam[1], lam[2]);
@@ -226,8 +228,9 @@ template int launch_poisson_block<float>(const fv_grid_s*, const float*, float*,
 // Dirichlet operator across (no-slip walls half a cell away); temperature uses cell-centred Dirichlet in
 // x (Eq. 4, homogeneous) and the Neumann operator in y and z (Eqs. 5-6), with s_T = 1/Pr.  No zero mode.
 // in and out may alias; tmp may not.
+// s != 0: (L_f - s I)^-1 instead (the eigenvalues of L_f are (lam_x + lam_y + lam_z) / s_f).
 template <typename R>
-int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp) {
+int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tmp, double s) {
   const FdmDev<R>* op[3];
   for (int d = 0; d < 3; ++d) {
     if (field < 3)
@@ -240,14 +243,14 @@ int launch_field_solve(const fv_grid_s* g, int field, const R* in, R* out, R* tm
   const int nx = g->nx, ny = g->ny, nz = g->nz;
   FV_TRY(pass_ops<R>(g, op[0]->Einv[0], nz, ny, nx, in, tmp, false, lam, false, 1.0));
   FV_TRY(pass_ops<R>(g, op[1]->Einv[1], nx, nz, ny, tmp, out, false, lam, false, 1.0));
-  FV_TRY(pass_ops<R>(g, op[2]->Einv[2], ny, nx, nz, out, tmp, true, lam, false, sfac));
+  FV_TRY(pass_ops<R>(g, op[2]->Einv[2], ny, nx, nz, out, tmp, true, lam, false, sfac, 1, s * sfac));
   FV_TRY(pass_ops<R>(g, op[0]->E[0], nz, ny, nx, tmp, out, false, lam, false, 1.0));
   FV_TRY(pass_ops<R>(g, op[1]->E[1], nx, nz, ny, out, tmp, false, lam, false, 1.0));
   FV_TRY(pass_ops<R>(g, op[2]->E[2], ny, nx, nz, tmp, out, false, lam, false, 1.0));
   return FV_OK;
 }
 
-template int launch_field_solve<double>(const fv_grid_s*, int, const double*, double*, double*);
-template int launch_field_solve<float>(const fv_grid_s*, int, const float*, float*, float*);
+template int launch_field_solve<double>(const fv_grid_s*, int, const double*, double*, double*, double);
+template int launch_field_solve<float>(const fv_grid_s*, int, const float*, float*, float*, double);
 
 }  // namespace fv

@@ -33,7 +33,7 @@ class fv_newton_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("krylov_tol", C.c_double),
                 ("max_newton", C.c_int), ("max_matvec", C.c_int), ("gmres_m", C.c_int),
                 ("gr_start", C.c_double), ("gr_ratio", C.c_double), ("precond", C.c_int),
-                ("forcing", C.c_int)]
+                ("forcing", C.c_int), ("ptc_dt0", C.c_double)]
 
 
 class fv_newton_report(C.Structure):

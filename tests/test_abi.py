@@ -52,5 +52,6 @@ def test_struct_layouts_match_header(libpath):
     # sizes derived from the C declarations (x86-64 / aarch64 LP64 ABI)
     from paper_2210_08816_gb300 import fv
     assert ctypes.sizeof(fv.fv_grid_desc) == 3 * 4 + 4 + 3 * 8 + 2 * 8
-    assert ctypes.sizeof(fv.fv_newton_opts) == 4 + 4 + 2 * 8 + 3 * 4 + 4 + 2 * 8 + 4 + 4  # precond, forcing
+    # precond, forcing, then the pseudo-time step (double)
+    assert ctypes.sizeof(fv.fv_newton_opts) == 4 + 4 + 2 * 8 + 3 * 4 + 4 + 2 * 8 + 4 + 4 + 8
     assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4
