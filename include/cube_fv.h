@@ -286,6 +286,15 @@ typedef struct {
     double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-3); the phase
                              also ends once its largest residual has not halved in 3 cycles */
     int low_max_restarts; /* FV_FP32: cycle cap of the FP32 phase (default 20) */
+    double euler_dt;      /* > 0: spectral transform by one implicit-Euler step in place of the
+                             Chebyshev polynomial: every cycle (the first included) runs its m
+                             Arnoldi steps on B = (I - euler_dt P J)^-1, applied by a BiCGstab(2)
+                             solve of (P J - I/euler_dt) y = x right-preconditioned with
+                             P (L - I/euler_dt)^-1 (to 0.01 tol in FP64, 1e-3 in the FP32 phase);
+                             eigenvalues still come from V^T A V and are tested with A itself.  B
+                             keeps the leading values of A near |mu| = 1/|1 - dt lam| and maps the
+                             stiff, convection-dominated far spectrum towards 0.  0 (default): the
+                             Chebyshev-preconditioned form of Section 1 */
 } fv_arnoldi_opts;
 
 typedef struct {

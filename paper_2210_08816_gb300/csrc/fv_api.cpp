@@ -1146,6 +1146,7 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->sigma = 0.0;
   o->low_tol = 1e-3;
   o->low_max_restarts = 20;
+  o->euler_dt = 0.0;
 }
 
 }  // extern "C"
@@ -1482,8 +1483,30 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
   // far end of the spectrum: Rayleigh quotient of a short power iteration (the Krylov spaces of B stop
   // showing it, and the Chebyshev polynomial grows fast outside its ellipse)
+  // implicit-Euler transform (euler_dt > 0): B = (I - dt P J)^-1 on the divergence-free subspace, applied as
+  // the solution y of (P J - I/dt) y = in (any scale: only the Krylov space matters, the Ritz values come
+  // from V^T A V) by BiCGstab(2) right-preconditioned with P (L - I/dt)^-1.  It maps the leading values to
+  // the largest |mu| = 1/|1 - dt lam| and the stiff, convection-dominated far spectrum towards 0, where a
+  // Chebyshev ellipse cannot separate them at high cell Peclet numbers.  Inexact solves only slow the
+  // convergence; the true residuals are taken with A itself.
+  const bool euler = o.euler_dt > 0.0;
+  DevBuf<R> ework, epre;
+  if (euler) {
+    FV_TRY(ework.alloc(7 * n));
+    FV_TRY(epre.alloc(n));
+  }
+  Operator<R> Ae{g, Gr, sigma, q, &mv};
+  Ae.pre = euler ? epre.p : nullptr;
+  Ae.s = euler ? 1.0 / o.euler_dt : 0.0;
+  const double etol = mixed ? 1e-3 : std::max(1e-12, 0.01 * o.tol);
+  auto apply_euler = [&](const R* in, R* out) -> int {
+    SolveInfo info;
+    FV_TRY(bicgstab2<R>(Ae, in, out, etol, 4000, ework.p, info));
+    FV_TRY(apply_precond<R>(g, out, epre.p, Ae.s));
+    return V.copy(out, epre.p);
+  };
   double lam_far = (carry && carry->lam_far != 0.0) ? carry->lam_far : 0.0;
-  if (lam_far == 0.0) {
+  if (lam_far == 0.0 && !euler) {
     R* z = y1.p;
     double zn2;
     FV_TRY(V.dot(x, x, &zn2));
@@ -1550,7 +1573,11 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     // ---- m Arnoldi steps (CGS2) on A (first cycle) or on B = p(A) from p(A) x: the restart vector's error
     // in the stiff directions would otherwise sit in v_1 alone, where no later Krylov vector of B (which
     // damps those directions) can cancel it, and every Ritz vector would inherit it
-    if (filt.on) {
+    if (euler) {
+      FV_TRY(V.copy(Vb.p, x));
+      FV_TRY(apply_euler(Vb.p, w.p));
+      x = w.p;
+    } else if (filt.on) {
       FV_TRY(V.copy(Vb.p, x));
       FV_TRY(apply_filter(Vb.p, w.p));
       x = w.p;
@@ -1562,7 +1589,9 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     int mm = m;
     for (int j = 0; j < m; ++j) {
       const R* vj = Vb.p + (size_t)j * n;
-      if (filt.on)
+      if (euler)
+        FV_TRY(apply_euler(vj, w.p));
+      else if (filt.on)
         FV_TRY(apply_filter(vj, w.p));
       else
         FV_TRY(A.apply(vj, w.p));
@@ -1590,7 +1619,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     }
     // ---- Rayleigh-Ritz matrix G = V^T A V (for a Krylov basis of A it is the Hessenberg matrix itself)
     G.assign((size_t)mm * mm, 0.0);
-    if (!filt.on) {
+    if (!filt.on && !euler) {
       for (int i = 0; i < mm; ++i)
         for (int j = 0; j < mm; ++j) G[(size_t)i * mm + j] = H[(size_t)i * m + j];
     } else {
@@ -1739,6 +1768,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     }
     // ---- next ellipse: wanted + guard Ritz values outside, the rest and the far end inside
     int nf = std::min(nw + o.guard, mm - 2);
+    if (euler) nf = 0;  // no filter to fit
     if (nf < mm && nf >= 1 && ritz[nf - 1].im > 0) ++nf;
     nf = std::max(nf, nw);
     std::vector<Ritz> wanted(ritz.begin(), ritz.begin() + nf), unwanted(ritz.begin() + nf, ritz.end());
@@ -1746,10 +1776,11 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     for (auto& u : unwanted) left = std::min(left, u.re);
     unwanted.push_back({1.05 * left, 0.0});
     double d = 0, c2 = 0, rate = 0;
-    best_ellipse(wanted, unwanted, d, c2, rate);
+    if (!euler) best_ellipse(wanted, unwanted, d, c2, rate);
     int deg = o.max_degree;
     if (rate > 1.0) deg = (int)std::ceil(std::log(kFilterGain) / std::log(rate));
     deg = std::max(o.min_degree, std::min(o.max_degree, deg));
+    if (euler) deg = 0;
     if (restart < 256) rep->degrees[restart] = deg;
     double lam_ref = -1e300;
     for (auto& wv : wanted) lam_ref = std::max(lam_ref, wv.re);
@@ -1853,7 +1884,7 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
   else
     fv_arnoldi_default_opts(&o);
   if (k < 1 || o.m > 200 || k + o.guard + 2 > o.m || o.min_degree < 1 || o.max_degree < o.min_degree ||
-      o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)))
+      o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)) || !(o.euler_dt >= 0.0))
     return invalid("bad Arnoldi options (need 1 <= k <= 63, k + guard + 2 <= m <= 200)");
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   fv_arnoldi_report rep;

@@ -46,7 +46,7 @@ class fv_arnoldi_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("m", C.c_int), ("tol", C.c_double), ("max_restarts", C.c_int),
                 ("max_degree", C.c_int), ("min_degree", C.c_int), ("guard", C.c_int),
                 ("seed", C.c_ulonglong), ("sigma", C.c_double), ("low_tol", C.c_double),
-                ("low_max_restarts", C.c_int)]
+                ("low_max_restarts", C.c_int), ("euler_dt", C.c_double)]
 
 
 class fv_arnoldi_report(C.Structure):

@@ -54,4 +54,4 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(fv.fv_grid_desc) == 3 * 4 + 4 + 3 * 8 + 2 * 8
     # precond, forcing, then the pseudo-time step (double)
     assert ctypes.sizeof(fv.fv_newton_opts) == 4 + 4 + 2 * 8 + 3 * 4 + 4 + 2 * 8 + 4 + 4 + 8
-    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8  # ..., euler_dt

@@ -146,6 +146,28 @@ def test_arnoldi_32cube_matches_stored_oracle_eigenvalues(fv, cube32):
     assert np.allclose(np.array(lam32[:len(ref)]), ref, rtol=1e-6, atol=0), (lam32, ref)
 
 
+def test_arnoldi_euler_transform_32cube_matches_stored_oracle_eigenvalues(fv, cube32):
+    """Arnoldi on the implicit-Euler propagator (I - dt P J)^-1 instead of the Chebyshev polynomial:
+    the same four leading eigenvalues of the 32^3, Gr = 1e5 workload as the oracle's stored ones (FP64
+    to 1e-8; the mixed form to 1e-6)."""
+    og, g, Gr, q, st, rep = cube32
+    assert st == fv.FV_OK
+    ref = _golden_eigs("config0_eigs_32.txt")
+    o = fv.fv_arnoldi_default_opts()
+    o.tol = 1e-9
+    o.euler_dt = 0.01
+    o.max_restarts = 20
+    st, lam, r64 = fv.arnoldi_leading(g, 4, Gr, q, o)
+    assert st == fv.FV_OK, (lam, list(r64.residual[:4]))
+    assert len(lam) == len(ref) and np.allclose(np.array(lam), ref, rtol=1e-8, atol=0), (lam, ref)
+    assert all(d == 0 for d in r64.degrees[:r64.restarts + 1])   # no Chebyshev filter ran
+    o.precision = fv.FV_FP32
+    o.tol = 1e-6
+    st, lam32, r32 = fv.arnoldi_leading(g, 4, Gr, q, o)
+    assert st == fv.FV_OK, (lam32, list(r32.residual[:4]))
+    assert np.allclose(np.array(lam32[:len(ref)]), ref, rtol=1e-6, atol=0), (lam32, ref)
+
+
 def test_arnoldi_fp64_gr0_closed_form(fv):
     shape = (10, 8, 6)
     og = D.Grid(*shape, stretch=0.0, Pr=PR)
