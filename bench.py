@@ -388,12 +388,7 @@ def finish(args, ws, rank, n, value, K, W, ms_step, e2e, launches, roof, hbm_ste
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{n}^3 tanh-stretched (s=1.5) cube, Gr=2e8, Pr=0.71: one Chebyshev-filter step "
-                               "(J.v + fast-diagonalisation projection + fused recurrence) + FP64 norm",
-                   "grid": [n, n, n], "stretch": STRETCH, "Gr": GR, "Pr": PR, "precision": "mixed (FP32 vectors, "
-                   "FP64 reductions)", "poisson": "direct fast diagonalisation (I_p = 1)",
-                   "l2": "inputs larger than L2 (268 MB per FP32 vector vs 129 MB L2)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": workload_config(n, ws), "precision": "mixed (FP32 vectors, FP64 reductions)",
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "hbm_stencil": hbm_stencil,
         "step_algorithmic_bytes": step_bytes, "kernel_breakdown": breakdown, "fp64_plain": fp64,
         "clocks": clocks,
@@ -541,8 +536,20 @@ def eigen_leg(fv, device):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+def workload_config(n, ws):
+    """The bench's workload, the same for both arms."""
+    return {"workload": f"{n}^3 tanh-stretched (s=1.5) cube, Gr=2e8, Pr=0.71: one Chebyshev-filter step "
+                        "(J.v + projection + recurrence) + FP64 norm",
+            "grid": [n, n, n], "stretch": STRETCH, "Gr": GR, "Pr": PR,
+            "poisson": "direct fast diagonalisation (I_p = 1)",
+            "l2": (f"inputs larger than L2 ({4 * n ** 3 * 4 / 1e6:.0f} MB per FP32 vector vs 129 MB L2)"
+                   if 4 * n ** 3 * 4 > 129e6 else "inputs fit in the 129 MB L2 (no flush between steps)"),
+            "parallelism": f"replicas x{ws}"}
+
+
 def oracle_step_seconds(n, reps=1):
-    """Time `reps` oracle J.v + projections (FP64 numpy) on the n^3 workload; returns seconds per step."""
+    """Time `reps` oracle steps (FP64 numpy) of the bench's workload: one step of the Chebyshev recurrence
+    y_b <- 2 t (A - d) y_a - c2 t t' y_b with A = P(J - sigma) + sigma, and its norm; seconds per step."""
     import numpy as np
     import oracle.discretisation as D
     from oracle.projection import Projector
@@ -551,17 +558,27 @@ def oracle_step_seconds(n, reps=1):
     P = Projector(og)
     q = D.from_api(og, seeded.normal_fields(100, og.shape, 50.0))
     q[3] = q[3] + (1.0 - og.axes[0].xc)[None, None, :]
-    v = D.from_api(og, seeded.normal_fields(101, og.shape))
+    ya = D.from_api(og, seeded.normal_fields(101, og.shape))
+    yb = D.from_api(og, seeded.normal_fields(102, og.shape))
+    hmin = min(float(np.min(a.dx)) for a in og.axes)
+    sigma = -0.5 * (1.0 / PR) * 3 * 4.0 / hmin ** 2
+    d, c2 = sigma, sigma * sigma * 0.9
+    s = 10.0 - d
+    tau = 1.0 / s
+    tn = 1.0 / (2.0 * s - c2 * tau)
     t0 = time.time()
     for _ in range(reps):
-        out = P.full(D.jvp_full(og, GR, q, v))
+        J = D.jvp_full(og, GR, q, ya)
+        Ay = P.full([J[c] - sigma * ya[c] for c in range(4)])
+        out = [2.0 * tn * (Ay[c] + (sigma - d) * ya[c]) - c2 * tau * tn * yb[c] for c in range(4)]
+        nrm = sum(float(np.sum(o * o)) for o in out)
     dt = (time.time() - t0) / reps
-    del out
+    del out, nrm
     return dt
 
 
 def cpu_baseline(n):
-    """The oracle timed on this host: one full n^3 J.v + projection in a single-threaded subprocess."""
+    """The oracle timed on this host: one full n^3 step of the workload in a single-threaded subprocess."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     try:
@@ -571,8 +588,9 @@ def cpu_baseline(n):
     except Exception as e:  # noqa: BLE001
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)[:200]}
     return {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full {n}^3 J.v + projection (FP64 numpy oracle, fast-diagonalisation solve), "
-                      f"{sec:.1f} s, single thread (BLAS threads = 1)", "cpu": cpu_model()}
+            "sample": f"one full {n}^3 step: J.v + projection + recurrence + norm (FP64 numpy oracle, "
+                      f"fast-diagonalisation solve), {sec:.1f} s, single thread (BLAS threads = 1)",
+            "cpu": cpu_model()}
 
 
 def cpu_model():
@@ -599,12 +617,11 @@ def reference_arm(args, ws, rank):
     value = 1.0 / sec
     threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
     cb = {"value": round(value, 5), "unit": UNIT, "cores": int(threads) if threads.isdigit() else os.cpu_count(),
-          "kind": "oracle", "sample": f"{K} full {n}^3 J.v + projections (FP64 numpy oracle)", "cpu": cpu_model()}
+          "kind": "oracle", "sample": f"{K} full {n}^3 steps (FP64 numpy oracle)", "cpu": cpu_model()}
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": K,
             "warmup": W, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{n}^3 tanh-stretched (s=1.5) cube, Gr=2e8, Pr=0.71: J.v + projection",
-                       "grid": [n, n, n]},
+            "config": workload_config(n, ws), "precision": "FP64 (numpy oracle)",
             "cpu_baseline": cb, "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
