@@ -108,11 +108,11 @@ def lib():
 
 
 EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
-            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot", "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
+            "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot",
+            "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
             "fv_get_tuning", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
-            "fv_newton_default_opts",
-            "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile", "fv_profile_read",
-            "fv_strerror", "fv_last_error"]
+            "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile",
+            "fv_profile_read", "fv_strerror", "fv_last_error"]
 
 FV_PROF_CLASSES = 7
 PROF_NAMES = ["stencil", "divergence", "transform", "correct", "reduce", "vector", "transform_tc"]

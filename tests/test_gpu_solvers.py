@@ -1,14 +1,16 @@
 """GPU Newton and Chebyshev-Arnoldi drivers (through the C-ABI) against the oracle.
 
-* FP64 Newton, with and without its optional diffusion preconditioner, reaches the oracle's steady state (both solve P F = 0 to round-off; the states agree
-  to 1e-9 in max-norm, the residual tolerance divided by the smallest eigenvalue magnitude).
+* FP64 Newton, with and without its optional diffusion preconditioner, reaches the oracle's steady
+  state (both solve P F = 0 to round-off; the states agree to 1e-9 in max-norm, the residual tolerance
+  divided by the smallest eigenvalue magnitude); so does pseudo-transient continuation, with no Gr ladder.
 * Mixed Newton (FP32 Krylov, FP64 residual) refines to the FP64 state within 1e-8 max-norm.
 * FP64 Arnoldi: Gr = 0 closed-form temperature spectrum, and agreement with the oracle's
   Chebyshev-Arnoldi at Gr > 0 (both converged to 1e-9 residual: eigenvalues to 1e-8).
 * Mixed Arnoldi: leading eigenvalue within 1e-6 of the FP64 one; its Ritz vectors certified by the
   oracle's own FP64 residual ||P J x - lam x|| / (|lam| ||x||).
 * The 32^3, Gr = 1e5 workload: GPU Newton, then the four leading eigenvalues of both forms against
-  the oracle's stored ones (tests/golden/config0_eigs_32.txt).
+  the oracle's stored ones (tests/golden/config0_eigs_32.txt), with the Chebyshev filter and with the
+  implicit-Euler transform.
 """
 import os
 
