@@ -27,7 +27,7 @@ def libpath():
     return build.build()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_hot_path_calls():
     d = _declared()
     for name in ("fv_residual", "fv_jvp", "fv_project", "fv_jvp_project", "newton_steady", "arnoldi_leading",
                  "fv_grid_create", "fv_grid_destroy", "fv_strerror"):
