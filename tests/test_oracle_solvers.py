@@ -6,8 +6,8 @@
 * At Gr = 0 about conduction, J is block triangular and the leading
   eigenvalues are the closed-form temperature-block values
   -(1/Pr) sum_d 4 n_d^2 sin^2(k_d pi / 2 n_d) (Dirichlet in x, Neumann in y, z).
-* At Gr > 0 the Arnoldi eigenvalues match a dense eigen-solve of P J restricted
-  to an orthonormal basis of the divergence-free subspace.
+* At Gr > 0 (12^3 stretched) the Arnoldi eigenvalues match a dense eigen-solve of P J
+  restricted to an orthonormal basis of the divergence-free subspace.
 * The filter's ellipse: its closed-form rightmost real point lies on its level curve, and the chosen
   ellipse stays left of the wanted values on the real axis.
 * On a normal matrix with a known, stiff spectrum (||A|| / |lam| ~ 500) the
@@ -98,7 +98,7 @@ def _dense_restricted(g, Gr, q):
     return lam[SV.order_eigs(lam)], Z
 
 
-def test_newton_then_arnoldi_match_dense_eigensolve():
+def test_newton_converges_quadratically_to_a_symmetric_state():
     g = D.Grid(8, 7, 6, stretch=1.5, Pr=PR)
     Gr = 1.2e4
     q, rep = SV.newton_steady(g, Gr, D.conduction_state(g), tol=1e-11)
@@ -111,7 +111,18 @@ def test_newton_then_arnoldi_match_dense_eigensolve():
     # the steady state keeps the three symmetries of Section 2
     assert max(DG.symmetry_measures(g, q[3])) <= 1e-9
     assert DG.nusselt_hot(g, q[3]) < -1.0
-    lam_dense, _ = _dense_restricted(g, Gr, q)
+
+
+def test_arnoldi_matches_dense_eigensolve_12cube():
+    """12^3 stretched, Gr = 2e4: the four leading eigenvalues of the Chebyshev-Arnoldi against numpy's
+    dense eigen-solve of Z^T (P J) Z (Z an orthonormal basis of the divergence-free subspace times T),
+    4753 x 4753.  About a minute on one core."""
+    g = D.Grid(12, 12, 12, stretch=1.5, Pr=PR)
+    Gr = 2.0e4
+    q, rep = SV.newton_steady(g, Gr, D.conduction_state(g), tol=1e-11)
+    assert rep["status"] == "converged"
+    lam_dense, Z = _dense_restricted(g, Gr, q)
+    assert Z.shape[1] == D.n_unknowns(g) - (12 ** 3 - 1)
     x0 = seeded.normal(2, 0, D.n_unknowns(g))
     lam, X, info = SV.leading_eigenvalues(g, Gr, q, k=4, m=20, seed_vector=x0, tol=1e-9)
     assert info["converged"]
