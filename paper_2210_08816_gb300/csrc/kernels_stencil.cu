@@ -377,9 +377,9 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait on an mbarrier phase; on expiry records code 16 in *err
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* err) {
-  for (int i = 0; i < (1 << 22); ++i)
+// bounded wait on an mbarrier phase (at most `spins` polls); on expiry records code 16 in *err
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* err, long long spins) {
+  for (long long i = 0; i < spins; ++i)
     if (bar_try(bar, parity)) return true;
   atomicCAS(err, 0, 16);
   return false;
@@ -390,7 +390,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* err
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
     k_stencil_z(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int use_tma,
-                int* err, Geo<R> g, int N, R Gr, R invPr, R sigma, const R* __restrict__ q, const R* __restrict__ v,
+                int* err, long long spins, Geo<R> g, int N, R Gr, R invPr, R sigma, const R* __restrict__ q, const R* __restrict__ v,
                 R* __restrict__ out) {
   constexpr int NA = (MODE == 0) ? 4 : 8;
   constexpr int AB = (MODE == 0) ? 0 : 4;
@@ -459,22 +459,27 @@ __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
   // plane kk lives in slot kk mod kRing; it is that slot's use number (kk - k0 + 1) / kRing
   auto wait_plane = [&](int kk) -> bool {
     if (!use_tma) return true;
-    return bar_wait(smem_addr(&bar[(kk + kRing) % kRing]), (uint32_t)(((kk - k0 + 1) / kRing) & 1), err);
+    return bar_wait(smem_addr(&bar[(kk + kRing) % kRing]), (uint32_t)(((kk - k0 + 1) / kRing) & 1), err, spins);
   };
   issue_plane(k0 - 1);
   issue_plane(k0);
   issue_plane(k0 + 1);
+  int issued = k0 + 1;  // last plane whose copy was started (the same value in every thread)
   if (!use_tma) cp_async_wait_all();
   __syncthreads();
   bool ok = wait_plane(k0 - 1);
   ok = wait_plane(k0) && ok;
+  ok = __syncthreads_and(ok);  // one decision for the whole CTA
   const int i = i0 + tx, j = j0 + ty;
   const bool active = (i < nx && j < ny);
   const R half = (MODE == 0) ? R(0.5) : R(1);
   const AxM<R> mx = load_axm(g, 0, active ? i : 0), my = load_axm(g, 1, active ? j : 0);
-  for (int k = k0; k < kend; ++k) {
-    if (k + 2 <= kend) issue_plane(k + 2);  // plane k+2 feeds the output plane k+1
-    const bool ready = wait_plane(k + 1) && ok;
+  for (int k = k0; k < kend && ok; ++k) {
+    if (k + 2 <= kend) {  // plane k+2 feeds the output plane k+1
+      issue_plane(k + 2);
+      issued = k + 2;
+    }
+    const bool ready = wait_plane(k + 1);
     if (active && ready) {
       const AxM<R> mz = load_axm(g, 2, k);
       Ring<R, NA> S;
@@ -533,8 +538,13 @@ __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
       }
     }
     if (!use_tma) cp_async_wait_all();  // plane k+2 has landed
-    __syncthreads();                    // nobody reads the slot of plane k-1 any more
+    ok = __syncthreads_and(ready);      // nobody reads the slot of plane k-1 any more; stop together
   }
+  // give-up path: every plane copy still in flight lands (waited for with the full limit) before the CTA
+  // exits, so that no bulk copy writes into shared memory the CTA no longer owns
+  if (!ok && use_tma && tid == 0)
+    for (int kk = max(k0 - 1, issued - kRing + 1); kk <= issued; ++kk)
+      bar_wait(smem_addr(&bar[(kk + kRing) % kRing]), (uint32_t)(((kk - k0 + 1) / kRing) & 1), err, 1LL << 22);
 }
 
 // rhs = D vel:  sum_d (vel_d(face p+1) - vel_d(face p)) / width, wall fluxes zero
@@ -841,7 +851,7 @@ int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, co
   if (use_tma && (state_map<R>(g, q, &tq) != FV_OK || state_map<R>(g, v, &tv) != FV_OK)) use_tma = 0;
   dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTY - 1) / kTY, (g->nz + kZChunk - 1) / kZChunk);
   ProfScope ps(g, PROF_STENCIL);
-  k_stencil_z<R, MODE><<<grid, kTX * kTY, smem, g->stream>>>(tq, tv, use_tma, g->ws.err, geo_of<R>(g), (int)g->N,
+  k_stencil_z<R, MODE><<<grid, kTX * kTY, smem, g->stream>>>(tq, tv, use_tma, g->ws.err, wait_spins(g), geo_of<R>(g), (int)g->N,
                                                              (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;

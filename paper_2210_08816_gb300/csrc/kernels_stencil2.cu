@@ -224,9 +224,9 @@ __device__ __forceinline__ bool bar_try2(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait on an mbarrier phase; on expiry records code 17 in *err
-__device__ __forceinline__ bool bar_wait2(uint32_t bar, uint32_t parity, int* err) {
-  for (long long i = 0; i < kPWaitLimit; ++i)
+// bounded wait on an mbarrier phase (at most `spins` polls); on expiry records code 17 in *err
+__device__ __forceinline__ bool bar_wait2(uint32_t bar, uint32_t parity, int* err, long long spins) {
+  for (long long i = 0; i < spins; ++i)
     if (bar_try2(bar, parity)) return true;
   atomicCAS(err, 0, 17);
   return false;
@@ -237,7 +237,7 @@ __device__ __forceinline__ bool bar_wait2(uint32_t bar, uint32_t parity, int* er
 template <bool BLOCK>
 __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
     k_stencil_pair(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int* err,
-                   Geo<float> g, int N, float Gr, float invPr, float sigma, float* __restrict__ out, int zc,
+                   long long spins, Geo<float> g, int N, float Gr, float invPr, float sigma, float* __restrict__ out, int zc,
                    int nch) {
   constexpr uint32_t kBox = 4u * kPL2 * sizeof(float);  // one state's box: 4 fields x kPHY x kPW2
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -285,21 +285,27 @@ __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
   };
   // plane kk lives in slot kk mod kPRing; it is that slot's use number (kk - k0 + 1) / kPRing
   auto wait_plane = [&](int kk) -> bool {
-    return bar_wait2(smem_addr2(&bar[(kk + kPRing) % kPRing]), (uint32_t)(((kk - k0 + 1) / kPRing) & 1), err);
+    return bar_wait2(smem_addr2(&bar[(kk + kPRing) % kPRing]), (uint32_t)(((kk - k0 + 1) / kPRing) & 1), err,
+                     spins);
   };
   issue_plane(k0 - 1);
   issue_plane(k0);
   issue_plane(k0 + 1);
+  int issued = k0 + 1;  // last plane whose copy was started (the same value in every thread)
   __syncthreads();
   bool ok = wait_plane(k0 - 1);
   ok = wait_plane(k0) && ok;
+  ok = __syncthreads_and(ok);  // one decision for the whole CTA
   const int x = i0 + 2 * tx, j = j0 + ty;
   const bool active = (x < nx && j < ny);  // nx is a multiple of kPX: both cells are in the domain
   const Bundle<float2> mx = load_bundle_pair(g, active ? x : 0);
   const Bundle<float2> my = broadcast(load_bundle(g, 1, active ? j : 0));
-  for (int k = k0; k < kend; ++k) {
-    if (k + 2 <= kend) issue_plane(k + 2);  // plane k+2 feeds the output plane k+1
-    const bool ready = wait_plane(k + 1) && ok;
+  for (int k = k0; k < kend && ok; ++k) {
+    if (k + 2 <= kend) {  // plane k+2 feeds the output plane k+1
+      issue_plane(k + 2);
+      issued = k + 2;
+    }
+    const bool ready = wait_plane(k + 1);
     if (active && ready) {
       const Bundle<float2> mz = broadcast(load_bundle(g, 2, k));
       Ring2 S;
@@ -325,8 +331,14 @@ __global__ void __launch_bounds__(kPX / 2 * kPY, 2)
       *reinterpret_cast<float2*>(out + 2 * N + o) = (k >= 1) ? r2 : zero;
       *reinterpret_cast<float2*>(out + 3 * N + o) = r3;
     }
-    __syncthreads();  // nobody reads the slot of plane k-1 any more
+    ok = __syncthreads_and(ready);  // nobody reads the slot of plane k-1 any more; stop together on a give-up
   }
+  // give-up path: every plane copy still in flight lands (waited for with the full limit) before the CTA
+  // exits, so that no bulk copy writes into shared memory the CTA no longer owns
+  if (!ok && tid == 0)
+    for (int kk = max(k0 - 1, issued - kPRing + 1); kk <= issued; ++kk)
+      bar_wait2(smem_addr2(&bar[(kk + kPRing) % kPRing]), (uint32_t)(((kk - k0 + 1) / kPRing) & 1), err,
+                kPWaitLimit);
 }
 
 // 4D tensor map of nvec FP32 states stored one after another (x, y, z, field; 4 nvec fields) with boxes
@@ -368,10 +380,10 @@ int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float
   dim3 grid(g->nx / kPX, (g->ny + kPY - 1) / kPY, nch * nvec);
   ProfScope ps(g, PROF_STENCIL);
   if (nvec > 1)
-    k_stencil_pair<true><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, g->geo32, (int)g->N, (float)Gr,
+    k_stencil_pair<true><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, wait_spins(g), g->geo32, (int)g->N, (float)Gr,
                                                                  (float)(1.0 / g->Pr), (float)sigma, out, zc, nch);
   else
-    k_stencil_pair<false><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, g->geo32, (int)g->N, (float)Gr,
+    k_stencil_pair<false><<<grid, kPX / 2 * kPY, smem, g->stream>>>(tq, tv, g->ws.err, wait_spins(g), g->geo32, (int)g->N, (float)Gr,
                                                                   (float)(1.0 / g->Pr), (float)sigma, out, zc, nch);
   FV_CUDA(cudaGetLastError());
   return FV_OK;

@@ -67,9 +67,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; on expiry records `code` in *err and returns false
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  for (long long i = 0; i < kWaitLimit; ++i)
+// bounded wait (at most `spins` polls); on expiry records `code` in *err and returns false
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                          long long spins = kWaitLimit) {
+  for (long long i = 0; i < spins; ++i)
     if (mbar_try(bar, parity)) return true;
   atomicCAS(err, 0, code);
   return false;
@@ -358,10 +359,10 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                     const __grid_constant__ CUtensorMap tmB1lo, const __grid_constant__ CUtensorMap tmB2hi,
                     const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int Ptot, int n,
                     const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
-                    int* err) {
+                    int* err, long long spins) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_conv[kTcStages], bar_empty[kTcStages];
-  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2];
+  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ float lz_s[256];
   const int h = n / 2;
@@ -383,6 +384,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       mbar_init(smem_u32(&bar_accf[b]), 1);
       mbar_init(smem_u32(&bar_acce[b]), 4);  // one arrival per epilogue warp
     }
+    mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (SCALE)
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         const int p0 = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM;
         for (int j = 0; j < nst; ++j) {
           const int gi = ti * nst + j, st = gi % kTcStages;
-          if (gi >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((gi / kTcStages) - 1) & 1, err, 11)) {
+          if (gi >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((gi / kTcStages) - 1) & 1, err, 11, spins)) {
             ok = false;
             break;
           }
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       }
       // drain: every issued copy has landed before the block may exit
       for (int gi = (issued > kTcStages ? issued - kTcStages : 0); gi < issued; ++gi)
-        mbar_wait(smem_u32(&bar_full[gi % kTcStages]), (gi / kTcStages) & 1, err, 12);
+        mbar_wait(smem_u32(&bar_full[gi % kTcStages]), (gi / kTcStages) & 1, err, 12, kWaitLimit);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       int last = -1;  // last tile whose accumulator commit was issued
       for (int ti = 0; ti < my_tiles && ok; ++ti) {
         const int b = ti & 1;
-        if (ti >= 2 && !mbar_wait(smem_u32(&bar_acce[b]), ((ti / 2) - 1) & 1, err, 13)) {
+        if (ti >= 2 && !mbar_wait(smem_u32(&bar_acce[b]), ((ti / 2) - 1) & 1, err, 13, spins)) {
           ok = false;
           break;
         }
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         const uint32_t dacc = tmem + (uint32_t)(b * 256);
         for (int j = 0; j < nst; ++j) {
           const int gi = ti * nst + j, st = gi % kTcStages;
-          if (!mbar_wait(smem_u32(&bar_conv[st]), (gi / kTcStages) & 1, err, 14)) {
+          if (!mbar_wait(smem_u32(&bar_conv[st]), (gi / kTcStages) & 1, err, 14, spins)) {
             ok = false;
             break;
           }
@@ -468,8 +470,13 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         mma_commit(smem_u32(&bar_accf[b]));  // arrives once every MMA issued so far has completed
         last = ti;
       }
-      // on an early exit, wait (bounded) for the MMAs already issued before the accumulators are freed
-      if (!ok && last >= 0) mbar_wait(smem_u32(&bar_accf[last & 1]), (last / 2) & 1, err, 16);
+      // give-up path: a commit after every MMA issued so far (including those of a tile left half done)
+      // arrives once they have all completed; wait for it (full limit) before the accumulators are freed
+      (void)last;
+      if (!ok) {
+        mma_commit(smem_u32(&bar_drain));
+        mbar_wait(smem_u32(&bar_drain), 0, err, 16, kWaitLimit);
+      }
     }
   } else if (warp < 6) {
     // converters: thread t owns row t of every stage's A tiles
@@ -479,7 +486,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
     for (int ti = 0; ti < my_tiles && ok; ++ti) {
       for (int j = 0; j < nst; ++j) {
         const int gi = ti * nst + j, st = gi % kTcStages;
-        if (!mbar_wait(smem_u32(&bar_full[st]), (gi / kTcStages) & 1, err, 17)) {
+        if (!mbar_wait(smem_u32(&bar_full[st]), (gi / kTcStages) & 1, err, 17, spins)) {
           ok = false;
           break;
         }
@@ -531,7 +538,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
     const int row = q * 32 + lane;
     for (int ti = 0; ti < my_tiles; ++ti) {
       const int b = ti & 1;
-      const bool ok = mbar_wait(smem_u32(&bar_accf[b]), (ti / 2) & 1, err, 18);
+      const bool ok = mbar_wait(smem_u32(&bar_accf[b]), (ti / 2) & 1, err, 18, spins);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // row pg of the stacked block: row p of field vec (fields of P x n, one after another)
@@ -794,14 +801,14 @@ int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float*
     const dim3 pgrid((unsigned)std::min<long long>(ntiles, g->tc.sms));
     if (bwd)
       k_transform_tcp<false, true><<<pgrid, kTcpThreads, smem, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err);
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     else if (scale)
       k_transform_tcp<true, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
           tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb,
-          g->ws.err);
+          g->ws.err, wait_spins(g));
     else
       k_transform_tcp<false, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err);
+          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     FV_CUDA(cudaGetLastError());
     return FV_OK;
   }
