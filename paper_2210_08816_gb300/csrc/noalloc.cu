@@ -36,6 +36,18 @@ struct ScratchAddr {
 ScratchAddr g_addr[kMaxDevices];
 std::mutex g_addr_mu;
 
+// A pointer the kernels on device `dev` may dereference: device memory of that device, or managed memory.
+// Host memory and another device's memory are refused: the kernels launch on the current device.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of a failed query
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 // Device address of the scratch array on the current device (host code must not use its name).
 int scratch_address(double** out) {
   int dev = 0;
@@ -123,6 +135,10 @@ extern "C" int fv_dot_noalloc(int prec, long long n, const void* a, const void* 
   if (!a || !b || !result) return FV_EINVAL;
   if (prec != FV_FP64 && prec != FV_FP32) return FV_EINVAL;
   if (n < 1 || n > kNoAllocMaxN) return FV_EINVAL;  // beyond the static scratch: 4096 blocks of 2^18 elements
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FV_ECUDA;
+  // a, b and result must live on the current device, where the kernels run
+  if (!on_device(a, dev) || !on_device(b, dev) || !on_device(result, dev)) return FV_EINVAL;
   double* scratch = nullptr;
   const int st = scratch_address(&scratch);
   if (st != FV_OK) return st;

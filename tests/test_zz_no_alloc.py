@@ -57,3 +57,38 @@ def test_noalloc_dot_rejects_bad_sizes(fv):
                             None) == fv.FV_EINVAL
     assert L.fv_dot_noalloc(5, 8, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), C.c_void_p(res.data_ptr()),
                             None) == fv.FV_EINVAL
+
+
+def test_noalloc_dot_more_blocks_than_the_finishing_threads(fv):
+    """FP32 vectors of 1100 * 2^18 elements (1.15 GB each): 1100 partial sums, more than the finishing
+    kernel's 1024 threads, so its strided loop runs; every slot is reduced (checked against a float64 sum
+    of the same products), on two calls in a row."""
+    n = 1100 * (1 << 18)
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda")
+    for call, seed in enumerate((5, 6)):
+        gen.manual_seed(seed)
+        a = torch.randn(n, dtype=torch.float32, device="cuda", generator=gen)
+        b = torch.randn(n, dtype=torch.float32, device="cuda", generator=gen)
+        ref = sum(float(torch.dot(a[i:i + (1 << 26)].double(), b[i:i + (1 << 26)].double()).item())
+                  for i in range(0, n, 1 << 26))
+        scale = sum(float(torch.sum(torch.abs(a[i:i + (1 << 26)].double() * b[i:i + (1 << 26)].double())).item())
+                    for i in range(0, n, 1 << 26))
+        fv.fv_dot_noalloc(fv.FV_FP32, a, b, res)
+        torch.cuda.synchronize()
+        got = float(res.item())
+        assert abs(got - ref) <= 1e-12 * scale, (call, got, ref)
+        del a, b
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_dot_rejects_host_memory(fv):
+    """A host pointer (or one the current device cannot dereference) is refused before any launch."""
+    import ctypes as C
+    h = np.zeros(8)
+    dres = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L = fv.lib()
+    hp = C.c_void_p(h.ctypes.data)
+    assert L.fv_dot_noalloc(0, 8, hp, hp, C.c_void_p(dres.data_ptr()), None) == fv.FV_EINVAL
+    a = torch.zeros(8, dtype=torch.float64, device="cuda")
+    assert L.fv_dot_noalloc(0, 8, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), hp, None) == fv.FV_EINVAL
