@@ -255,18 +255,23 @@ def gpu_arm(args, ws, rank, local):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     if dom == "transform_tc":
-        # algorithmic FLOPs of one pass: an n x n matrix applied along one axis of an N-cell field
-        flops = 2.0 * N * n
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 * (1.1 / 2.25)   # TF32 dense = bf16 dense x nominal ratio 1.1 / 2.25 PFLOP/s
-        roof = {"kernel": "k_transform_tc (tcgen05 fast-diagonalisation pass, 3 x TF32 split)", "bound": "tensor",
-                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4),
-                "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if "bf16_tflops" in peaks
-                                else "fallback 1.9 PF bf16 x 1.1/2.25"),
-                "executed_tflops": round(3 * achieved, 2)}
+        # One pass reads the N-cell field and writes it with the contracted axis rotated: 2 N FP32 values of
+        # HBM traffic, which bounds it.  Its tensor work: the grid is mirror-symmetric, so a pass contracts
+        # the sums and differences of mirrored inputs with two n/2 x n/2 matrices, N n flops (half of the
+        # dense 2 N n), executed three times as 3 x TF32.
         traffic_bytes = 2 * N * 4
+        achieved = traffic_bytes / (per_launch_ms * 1e-3) / 1e9
+        flops = 1.0 * N * n
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        tf32_peak = bf16 * (1.1 / 2.25)   # TF32 dense = bf16 dense x nominal ratio 1.1 / 2.25 PFLOP/s
+        executed = 3.0 * flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_transform_tcp (tcgen05 fast-diagonalisation pass, 3 x TF32 split)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_source": hbm_src,
+                "tensor": {"executed_tflops": round(executed, 2), "peak": round(tf32_peak, 1),
+                           "frac": round(executed / tf32_peak, 4), "flops_per_pass": 3 * flops,
+                           "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if "bf16_tflops" in peaks
+                                           else "fallback 1.9 PF bf16 x 1.1/2.25")}}
     elif dom == "transform":
         flops = 2.0 * N * n
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
@@ -352,6 +357,7 @@ def e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream):
 
     run(4)
     torch.cuda.synchronize()
+    link = host_link(host_in[0], d_in[0], host_out[0], d_out[0], stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(ws)
     e0.record(stream)
@@ -363,9 +369,31 @@ def e2e_leg(fv, g, q, ya, yb, sigma, K, ws, device, stream):
     e_ms = max_over_ranks(ws, e0.elapsed_time(e1), device)
     e2e = {"value": round(ws * Ke / (e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": nb * ya.element_size(),
            "d2h_bytes_per_step": nb * yb.element_size(), "steps": Ke,
-           "pipeline": "upload of step i+1 and download of step i-1 overlap step i (3 streams, 2 buffer pairs)"}
+           "pipeline": "upload of step i+1 and download of step i-1 overlap step i (3 streams, 2 buffer pairs)",
+           "host_link": link}
     del host_in, host_out, d_in, d_out
     return e2e
+
+
+def host_link(h_in, d_in, h_out, d_out, stream, reps=3):
+    """Bandwidth of the host link on this machine for the e2e leg's buffers: one pinned H2D and one pinned D2H copy
+    of a step's vector, each timed alone with CUDA events (best of `reps`), so that the e2e figure can be
+    read against what the link allows."""
+    import torch
+    best = {"h2d": 1e30, "d2h": 1e30}
+    for _ in range(reps):
+        for k, (dst, src) in (("h2d", (d_in, h_in)), ("d2h", (h_out, d_out))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            best[k] = min(best[k], e0.elapsed_time(e1))
+    nbytes = h_in.numel() * h_in.element_size()
+    return {"pinned": bool(h_in.is_pinned() and h_out.is_pinned()), "bytes": nbytes,
+            "h2d_gbs": round(nbytes / (best["h2d"] * 1e-3) / 1e9, 1),
+            "d2h_gbs": round(nbytes / (best["d2h"] * 1e-3) / 1e9, 1),
+            "step_bound_per_s": round(1.0 / max(best["h2d"], best["d2h"]) * 1e3, 1)}
 
 
 def fp64_leg(fv, g, q64, y0_64, y1_64, sigma, K, ws, device, stream):
