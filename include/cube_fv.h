@@ -81,6 +81,19 @@ int fv_set_stream(fv_grid g, void* stream);
 /* Number of elements of one state/vector buffer: 4*nx*ny*nz. */
 long long fv_state_elems(fv_grid g);
 
+/* Failure detection (no counterpart in the paper).  Every wait of the library's kernels on an mbarrier
+ * (the TMA plane ring of the J.v stencils, the pipeline of the tensor-core pressure-solve passes) polls at
+ * most `spins` times; a wait that runs out records a code in the handle's device error word, the kernel
+ * stops issuing work, lets every bulk copy and tensor-core operation it has started complete, releases its
+ * tensor memory and returns (its outputs are then undefined).  spins < 0 restores the default (2^22 polls,
+ * seconds); 0 makes every such wait give up at once, which is how the give-up path is exercised.
+ * Errors: FV_EINVAL (null handle). */
+int fv_set_wait_limit(fv_grid g, long long spins);
+/* Synchronise the handle's stream and report a device-side wait that gave up since the last check as
+ * FV_ETIMEOUT (clearing it); the handle stays usable.  Calls that return host scalars make the same check.
+ * Errors: FV_EINVAL, FV_ECUDA, FV_ETIMEOUT. */
+int fv_sync(fv_grid g);
+
 /* Residual F(q; Gr) of Eqs. 1-2 without the pressure gradient (Section 2),
  * FP64 always: F_u = -div(u u) + Lap u, F_w additionally + Gr T_face,
  * F_T = -div(u T) + Lap T / Pr with the Dirichlet data of Eq. 4.
@@ -207,6 +220,16 @@ int fv_batch_plan_destroy(fv_batch_plan plan);
  * alias.  Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM (workspace). */
 int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out);
 
+/* Transfer of an FP64 state between two grids of the cube (grid sequencing: a coarse steady state as the
+ * Newton start on a finer grid; Section 4.1 refines its grids from 100^3 to 256^3 and continues solutions
+ * between neighbouring states).  Every field is interpolated trilinearly in physical coordinates, with the
+ * wall values of Eqs. 4-6 at the ends of each axis (no-slip velocity 0; T = 1 and 0 on the x-walls; zero
+ * flux on the others: constant beyond the first and last centre); the velocity is then projected on the
+ * target grid so that it is discretely divergence free.  q_from: device double[4 N_from], q_to: device
+ * double[4 N_to] (must not alias); runs on the target handle's stream after synchronising the source's.
+ * Both handles must belong to the current device.  Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
+int fv_transfer(fv_grid from, const double* q_from, fv_grid to, double* q_to);
+
 /* Element-type conversion of a state: FP64 -> FP32 (to_fp32 = 1) or back. */
 int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst);
 
@@ -272,8 +295,9 @@ typedef struct {
     int precision;        /* FV_FP64, or FV_FP32: a phase with FP32 Krylov vectors and
                              J.v + projection (FP64 Rayleigh-Ritz matrix, Gram-Schmidt
                              coefficients and inner products) down to residual low_tol, then
-                             FP64 cycles started from its Ritz vectors, with the polynomial
-                             degree capped at max_degree / 8, refine to tol */
+                             FP64 cycles started from its Ritz vectors refine to tol (each FP64
+                             cycle picks its polynomial degree by the same rule as the FP32
+                             ones, clamped to [min_degree, max_degree]) */
     int m;                /* Krylov subspace dimension per cycle */
     double tol;           /* stop when every wanted Ritz pair has
                              ||A x - lam x|| <= tol |lam| ||x|| (true residual, FP64 reductions) */
@@ -288,13 +312,20 @@ typedef struct {
     int low_max_restarts; /* FV_FP32: cycle cap of the FP32 phase (default 20) */
     double euler_dt;      /* > 0: spectral transform by one implicit-Euler step in place of the
                              Chebyshev polynomial: every cycle (the first included) runs its m
-                             Arnoldi steps on B = (I - euler_dt P J)^-1, applied by a BiCGstab(2)
-                             solve of (P J - I/euler_dt) y = x right-preconditioned with
-                             P (L - I/euler_dt)^-1 (to 0.01 tol in FP64, 1e-3 in the FP32 phase);
+                             Arnoldi steps on B = (I - euler_dt P J)^-1, applied by a restarted
+                             GMRES solve of (P J - I/euler_dt) y = x right-preconditioned with
+                             P (L - I/euler_dt)^-1 (inner_m, inner_max, inner_tol below);
                              eigenvalues still come from V^T A V and are tested with A itself.  B
                              keeps the leading values of A near |mu| = 1/|1 - dt lam| and maps the
                              stiff, convection-dominated far spectrum towards 0.  0 (default): the
                              Chebyshev-preconditioned form of Section 1 */
+    int inner_m;          /* euler_dt > 0: restart length of the GMRES shifted solves (default 50) */
+    int inner_max;        /* euler_dt > 0: J.v + projections per shifted solve (default 3000) */
+    double inner_tol;     /* euler_dt > 0: relative residual of each shifted solve; 0 (default): 1e-9
+                             for FP64 solves, 1e-3 for FP32 ones (about their round-off floor).  In
+                             the FP64 cycles of the mixed form every shifted solve is FP64-accurate
+                             by iterative refinement: FP64 residual x - (I - dt P J) y, FP32 GMRES
+                             correction to 1e-3, until the FP64 residual is below inner_tol */
 } fv_arnoldi_opts;
 
 typedef struct {
@@ -308,6 +339,10 @@ typedef struct {
     double seconds;
     int restarts_low;     /* FV_FP32: cycles of the FP32 phase (included in restarts) */
     long long matvecs_low;/* FV_FP32: J.v + projections of the FP32 phase (included in matvecs) */
+    long long matvecs_fp64;  /* J.v + projections in FP64 (included in matvecs); the rest ran in FP32 */
+    int solves;           /* euler_dt > 0: shifted solves */
+    int solves_short;     /* euler_dt > 0: shifted solves that stopped above their tolerance */
+    double solve_worst;   /* euler_dt > 0: largest final relative residual of a shifted solve */
 } fv_arnoldi_report;
 
 void fv_arnoldi_default_opts(fv_arnoldi_opts* o);

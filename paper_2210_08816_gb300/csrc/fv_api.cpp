@@ -715,6 +715,26 @@ int fv_set_stream(fv_grid g, void* stream) {
 
 long long fv_state_elems(fv_grid g) { return g ? (long long)(4 * g->N) : -1; }
 
+int fv_set_wait_limit(fv_grid g, long long spins) {
+  if (!g) return invalid("null handle");
+  g->wait_spins = spins < 0 ? -1 : spins;
+  return FV_OK;
+}
+
+int fv_sync(fv_grid g) {
+  if (!g) return invalid("null handle");
+  int dev_err = 0;
+  FV_CUDA(cudaMemcpyAsync(&dev_err, g->ws.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  if (dev_err != 0) {
+    FV_CUDA(cudaMemsetAsync(g->ws.err, 0, sizeof(int), g->stream));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    set_error("a bounded device-side wait expired (code " + std::to_string(dev_err) + ")");
+    return FV_ETIMEOUT;
+  }
+  return FV_OK;
+}
+
 int fv_profile(fv_grid g, int enable) {
   if (!g) return invalid("null grid");
   FV_CUDA(cudaStreamSynchronize(g->stream));
@@ -1040,6 +1060,15 @@ int fv_batch_plan_destroy(fv_batch_plan plan) {
   return FV_OK;
 }
 
+int fv_transfer(fv_grid from, const double* q_from, fv_grid to, double* q_to) {
+  if (!from || !to || !q_from || !q_to) return invalid("null argument");
+  if ((const void*)q_from == (const void*)q_to) return invalid("q_to must not alias q_from");
+  FV_TRY(ensure_ws<double>(to));
+  FV_CUDA(cudaStreamSynchronize(from->stream));  // q_from is complete before the other stream reads it
+  FV_TRY(launch_prolong(from, q_from, to, q_to));
+  return project_inplace<double>(to, q_to, 1, 0.0, nullptr, nullptr);
+}
+
 int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out) {
   if (!g || !in || !out) return invalid("null argument");
   if (prec == FV_FP64) return diffusion_solve<double>(g, (const double*)in, (double*)out);
@@ -1147,6 +1176,9 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->low_tol = 1e-3;
   o->low_max_restarts = 20;
   o->euler_dt = 0.0;
+  o->inner_m = 50;
+  o->inner_max = 3000;
+  o->inner_tol = 0.0;
 }
 
 }  // extern "C"
@@ -1425,6 +1457,73 @@ static void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz
   }
 }
 
+// Statistics of the shifted solves of the implicit-Euler transform.
+struct SolveStats {
+  int solves = 0, short_ = 0;
+  double worst = 0.0;
+  void note(bool converged, double rel) {
+    ++solves;
+    if (!converged) ++short_;
+    worst = std::max(worst, rel);
+  }
+};
+
+// FP64-accurate shifted solve (P J - s) y = x by iterative refinement around FP32 GMRES: the residual
+// x - (A - s) y is formed with FP64 products, normalised, solved in FP32 (right-preconditioned GMRES to
+// tol32), and the FP32 correction, re-projected in FP64, is added in FP64.  Each round gains the FP32
+// solve's digits (~3) at one FP64 product and one FP64 projection; the stiff directions never see FP32
+// round-off in y, because every correction passes through M^-1 = P (L - s)^-1 and the FP64 residual.
+struct EulerRefine {
+  fv_grid_s* g = nullptr;
+  double Gr = 0.0, sigma = 0.0, s = 0.0;
+  const float* q32 = nullptr;
+  const double* q64 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *pre32 = nullptr, *basis32 = nullptr, *w32 = nullptr;
+  double *r64 = nullptr, *t64 = nullptr;
+  int inner_m = 50, inner_max = 3000, max_outer = 8;
+  double tol32 = 1e-3, tol64 = 1e-9;
+  long long* mv64 = nullptr;
+  long long mv32 = 0;
+  SolveStats* stats = nullptr;
+
+  int solve(const double* in, double* out) {
+    const size_t n = 4 * g->N;
+    Vec<double> V64{g, n};
+    Vec<float> V32{g, n};
+    Operator<float> A32{g, Gr, sigma, q32, &mv32};
+    A32.pre = pre32;
+    A32.s = s;
+    Operator<double> A64{g, Gr, sigma, q64, mv64};
+    A64.s = s;
+    FV_TRY(V64.zero(out));
+    FV_TRY(V64.copy(r64, in));
+    double xn2;
+    FV_TRY(V64.dot(in, in, &xn2));
+    const double xn = std::sqrt(xn2);
+    double rel = 1.0;
+    for (int it = 0; it <= max_outer; ++it) {
+      double rn2;
+      FV_TRY(V64.dot(r64, r64, &rn2));
+      const double rn = std::sqrt(rn2);
+      rel = xn > 0.0 ? rn / xn : 0.0;
+      if (rel <= tol64 || it == max_outer) break;
+      FV_TRY(V64.lin(t64, {{1.0 / rn, r64}}));
+      FV_TRY(launch_convert(g, n, t64, b32));
+      FV_TRY(V32.zero(x32));
+      SolveInfo info;
+      FV_TRY(gmres<float>(A32, b32, x32, tol32, inner_m, inner_max, basis32, w32, info));
+      FV_TRY(apply_precond<float>(g, x32, pre32, s));
+      FV_TRY(launch_convert(g, n, pre32, t64));
+      FV_TRY(project_inplace<double>(g, t64, 1, 0.0, nullptr, nullptr));
+      FV_TRY(V64.lin(out, {{1.0, out}, {rn, t64}}));
+      FV_TRY(A64.apply(out, t64));
+      FV_TRY(V64.lin(r64, {{1.0, in}, {-1.0, t64}}));
+    }
+    if (stats) stats->note(rel <= tol64, rel);
+    return FV_OK;
+  }
+};
+
 // Chebyshev polynomial p(z) = T_deg((z - d)/c) / T_deg((lam_ref - d)/c) of one cycle's ellipse.
 struct ChebFilter {
   bool on = false;
@@ -1450,10 +1549,400 @@ constexpr double kFilterGain = 1e2;
 // component (relative weight tol / 100) under the next ellipse.
 // stall > 0: give up (FV_ENOCONV, Ritz vectors still written) once the largest relative residual has not
 // halved over `stall` cycles (the FP32 phase of the mixed form stops at its round-off floor).
+// Shift-invert Arnoldi for the implicit-Euler transform, with thick restarts.
+//
+// B = (A - s I)^-1, s = 1 / euler_dt, on the divergence-free subspace (A = P (J - sigma) + sigma): an
+// eigenvalue lam of A is mu = 1 / (lam - s) of B, so the eigenvalues nearest s (the rightmost ones for a
+// shift right of the spectrum) have the largest |mu| and the stiff, convection-dominated far spectrum maps
+// to |mu| ~ 0.  The Arnoldi process runs on B (each application one GMRES solve of (A - s) y = x,
+// right-preconditioned with P (L - s)^-1), and the Ritz pairs are those of B: extremal eigenvalues of B,
+// which Rayleigh-Ritz approximates reliably even for this far-from-normal operator (a Rayleigh-Ritz
+// extraction with A itself can return values from the field of values of A far right of any eigenvalue).
+// The eigenvalue of A reported for a Ritz vector x is its Rayleigh quotient x^H A x / x^H x, and the
+// residual ||A x - lam x|| / (|lam| ||x||) is taken with A.
+//
+// Restart (thick, Krylov-Schur style): B V_m = V_m G + v_m g^T holds for the basis V_m and the projected
+// matrix G (not Hessenberg after the first restart).  The Ritz vectors of the p Ritz values of largest
+// |mu|, orthonormalised in coefficient space (Y = Q_y R, G Q_y = Q_y (Q_y^T G Q_y) because span Y is
+// G-invariant), give the new leading basis V_m Q_y with projected block Q_y^T G Q_y, followed by v_m with
+// the row g^T Q_y; the Arnoldi process then expands from v_m.  Inexact solves perturb this relation at
+// their tolerance, which is relaxed while the residuals are large (1e-3 of the previous cycle's largest,
+// within [floor, 1e-2]).
+template <typename R>
+static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
+                      double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start, int stall,
+                      EulerRefine* refine) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t n = 4 * g->N;
+  const int m = o.m;
+  const bool mixed = !std::is_same<R, double>::value;
+  const double sigma = (o.sigma != 0.0) ? o.sigma : g->sigma_default;
+  const double s = 1.0 / o.euler_dt;
+  const bool refined = refine != nullptr && std::is_same<R, double>::value;
+  // Ritz values kept over a restart (largest |mu|) and reported (the k of largest real part among them)
+  const int keep_max = std::max(1, std::min(m - 2, std::max(k + o.guard, 2 * k)));
+  DevBuf<R> qR, Vb, w, y0, y1, X;
+  if (mixed) {
+    FV_TRY(qR.alloc(n));
+    FV_TRY(launch_convert(g, n, q64, (float*)qR.p));
+  }
+  const R* q = mixed ? qR.p : (const R*)q64;
+  FV_TRY(Vb.alloc((size_t)(m + 1) * n));
+  FV_TRY(w.alloc(n));
+  FV_TRY(y0.alloc(n));
+  FV_TRY(y1.alloc(n));
+  FV_TRY(X.alloc((size_t)(keep_max + 2) * n));
+  Vec<R> V{g, n};
+  long long mv = 0;
+  Operator<R> A{g, Gr, sigma, q, &mv};
+  DevBuf<R> gbasis, gw, epre;
+  if (!refined) {
+    FV_TRY(gbasis.alloc((size_t)(o.inner_m + 1) * n));
+    FV_TRY(gw.alloc(n));
+    FV_TRY(epre.alloc(n));
+  }
+  Operator<R> Ae{g, Gr, sigma, q, &mv};
+  Ae.pre = epre.p;
+  Ae.s = s;
+  double etol = 1e-3;
+  SolveStats sstats;
+  if (refined) {
+    refine->stats = &sstats;
+    refine->mv64 = &mv;  // the refinement's FP64 products count with this run's
+  }
+  auto apply_B = [&](const R* in, R* out) -> int {
+    if constexpr (std::is_same<R, double>::value) {
+      if (refined) return refine->solve(in, out);
+    }
+    FV_TRY(V.zero(out));
+    SolveInfo info;
+    FV_TRY(gmres<R>(Ae, in, out, etol, o.inner_m, o.inner_max, gbasis.p, gw.p, info));
+    sstats.note(info.status == FV_OK, info.rel);
+    FV_TRY(apply_precond<R>(g, out, epre.p, s));
+    return V.copy(out, epre.p);
+  };
+  // CGS2 of w against Vb[0, j]: coefficients added to column `col` of Gb; returns ||w|| after
+  std::vector<double> Gb((size_t)(m + 1) * m, 0.0), h(m + 1);
+  auto orthogonalise = [&](R* wv, int j, int col, double* norm) -> int {
+    for (int pass = 0; pass < 2; ++pass) {
+      FV_TRY(launch_multidot<R>(g, Vb.p, n, j + 1, wv, n, 1));
+      FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, j + 1, g->ws.scalars + 1, wv, n));
+      FV_TRY(read_scalars(g, 1, j + 1, h.data()));
+      for (int i = 0; i <= j; ++i) {
+        if (!std::isfinite(h[i])) {
+          set_error("non-finite Gram-Schmidt coefficient");
+          return FV_ENAN;
+        }
+        if (col >= 0) Gb[(size_t)i * m + col] += h[i];
+      }
+    }
+    double n2;
+    FV_TRY(V.dot(wv, wv, &n2));
+    *norm = std::sqrt(n2);
+    return FV_OK;
+  };
+  // start vector: seeded N(0,1) (or the caller's), projected, then one application of B (damps its stiff
+  // components, which no later Krylov vector of B could cancel)
+  R* x = y0.p;
+  if (start) {
+    FV_TRY(V.copy(x, start));
+  } else {
+    FV_TRY(launch_fill_normal<R>(g, o.seed, x));
+  }
+  FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
+  const double etol_floor = o.inner_tol > 0.0 ? o.inner_tol : (mixed ? 1e-3 : std::max(1e-12, 0.01 * o.tol));
+  double worst_prev = 1.0, best = 1e300;
+  int best_at = 0, p = 0, status = FV_ENOCONV, nret = 0;
+  std::vector<double> Gm, Hg, Qg, hre, him, sh;
+  for (int restart = 0; restart <= o.max_restarts; ++restart) {
+    etol = std::min(1e-2, std::max(etol_floor, 1e-3 * worst_prev));
+    if (refined) refine->tol64 = etol;
+    if (p == 0) {  // fresh start: v_0 = B x / ||B x||
+      std::fill(Gb.begin(), Gb.end(), 0.0);
+      FV_TRY(apply_B(x, w.p));
+      double xn2;
+      FV_TRY(V.dot(w.p, w.p, &xn2));
+      const double xn = std::sqrt(xn2);
+      if (!(xn > 0.0)) {
+        set_error("shift-invert Arnoldi: zero start vector");
+        return FV_ENOCONV;
+      }
+      FV_TRY(V.lin(Vb.p, {{1.0 / xn, w.p}}));
+    }
+    // ---- expand columns p .. m-1: B v_j = sum_i G[i][j] v_i + G[j+1][j] v_{j+1}
+    int mm = m;
+    for (int j = p; j < m; ++j) {
+      FV_TRY(apply_B(Vb.p + (size_t)j * n, w.p));
+      double wn;
+      FV_TRY(orthogonalise(w.p, j, j, &wn));
+      double colmax = 0.0;
+      for (int i = 0; i <= j; ++i) colmax = std::max(colmax, std::fabs(Gb[(size_t)i * m + j]));
+      if (wn <= 1e-14 * colmax || wn == 0.0) {
+        // the space is invariant under B: continue with a random direction that B does not couple in
+        Gb[(size_t)(j + 1) * m + j] = 0.0;
+        FV_TRY(launch_fill_normal<R>(g, o.seed + 7919ULL * (unsigned long long)(restart * (m + 1) + j + 1), w.p));
+        FV_TRY(project_inplace<R>(g, w.p, 1, 0.0, nullptr, nullptr));
+        FV_TRY(orthogonalise(w.p, j, -1, &wn));
+        if (!(wn > 0.0)) {
+          mm = j + 1;
+          break;
+        }
+      } else {
+        Gb[(size_t)(j + 1) * m + j] = wn;
+      }
+      FV_TRY(V.lin(Vb.p + (size_t)(j + 1) * n, {{1.0 / wn, w.p}}));
+    }
+    // ---- Ritz values of B: eigenvalues of G (mm x mm)
+    Gm.assign((size_t)mm * mm, 0.0);
+    for (int i = 0; i < mm; ++i)
+      for (int j = 0; j < mm; ++j) Gm[(size_t)i * mm + j] = Gb[(size_t)i * m + j];
+    Hg = Gm;
+    hessenberg_reduce(mm, Hg, Qg);
+    if (!hessenberg_eigvals(mm, Hg.data(), mm, hre, him)) {
+      set_error("Hessenberg QR did not converge");
+      return FV_ENOCONV;
+    }
+    struct Mu {
+      double re, im;
+    };
+    std::vector<Mu> mus;
+    {
+      std::vector<bool> used(mm, false);
+      for (int i = 0; i < mm; ++i) {
+        if (used[i]) continue;
+        used[i] = true;
+        if (him[i] == 0.0) {
+          mus.push_back({hre[i], 0.0});
+          continue;
+        }
+        int bj = -1;
+        double bd = 1e300;
+        for (int j2 = 0; j2 < mm; ++j2)
+          if (!used[j2] && him[j2] * him[i] < 0.0) {
+            const double dd = std::hypot(hre[j2] - hre[i], him[j2] + him[i]);
+            if (dd < bd) {
+              bd = dd;
+              bj = j2;
+            }
+          }
+        if (bj >= 0) {
+          used[bj] = true;
+          const double r = 0.5 * (hre[i] + hre[bj]), a = 0.5 * (std::fabs(him[i]) + std::fabs(him[bj]));
+          mus.push_back({r, a});
+        } else {
+          mus.push_back({hre[i], std::fabs(him[i])});
+        }
+      }
+    }
+    // one entry per real value or conjugate pair (+Im); order by |mu| descending
+    std::sort(mus.begin(), mus.end(),
+              [](const Mu& a, const Mu& b) { return std::hypot(a.re, a.im) > std::hypot(b.re, b.im); });
+    // kept: the largest |mu| filling at most keep_max real slots (a pair takes two)
+    std::vector<Mu> kept;
+    int slots = 0;
+    for (const Mu& u : mus) {
+      const int need = u.im != 0.0 ? 2 : 1;
+      if (slots + need > keep_max) break;
+      kept.push_back(u);
+      slots += need;
+    }
+    if (kept.empty()) kept.push_back(mus[0]);
+    // reported: the k (real slots, a pair completed) of largest real part of lam = s + 1/mu among the kept
+    auto lam_of = [&](const Mu& u) {
+      const std::complex<double> l = s + 1.0 / std::complex<double>(u.re, u.im);
+      return l;
+    };
+    std::vector<int> ord(kept.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam_of(kept[a]).real() > lam_of(kept[b]).real(); });
+    std::vector<int> rep_idx;
+    int rslots = 0;
+    for (int i : ord) {
+      if (rslots >= k) break;
+      rep_idx.push_back(i);
+      rslots += kept[i].im != 0.0 ? 2 : 1;
+    }
+    // ---- eigenvectors of G for the kept values: columns of Y (real, and imaginary part of a pair)
+    std::vector<std::vector<double>> Ycols;   // mm each
+    std::vector<int> first_col(kept.size());
+    for (size_t i = 0; i < kept.size(); ++i) {
+      if (!hessenberg_eigvec(mm, Hg.data(), mm, kept[i].re, kept[i].im, sh)) {
+        set_error("Ritz vector inverse iteration failed");
+        return FV_ENOCONV;
+      }
+      std::vector<double> yr(mm, 0.0), yi(mm, 0.0);
+      for (int r = 0; r < mm; ++r)
+        for (int c = 0; c < mm; ++c) {
+          yr[r] += Qg[(size_t)r * mm + c] * sh[2 * c];
+          yi[r] += Qg[(size_t)r * mm + c] * sh[2 * c + 1];
+        }
+      first_col[i] = (int)Ycols.size();
+      Ycols.push_back(yr);
+      if (kept[i].im != 0.0) Ycols.push_back(yi);
+    }
+    // ---- reported Ritz vectors x = V y into X (slot: Re, then Im of a pair), Rayleigh quotients and
+    // true residuals with A
+    auto combine = [&](const std::vector<double>& y, R* dst) -> int {
+      std::vector<double> c(mm);
+      for (int t = 0; t < mm; ++t) c[t] = -y[t];
+      FV_CUDA(cudaMemcpyAsync(g->ws.scalars + 1, c.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, g->stream));
+      FV_TRY(V.zero(dst));
+      FV_TRY(launch_subtract_basis<R>(g, Vb.p, n, mm, g->ws.scalars + 1, dst, n));
+      FV_CUDA(cudaStreamSynchronize(g->stream));
+      return FV_OK;
+    };
+    struct Pair {
+      double lr, li, res, xn;
+      int slot;
+    };
+    std::vector<Pair> pairs;
+    int slot = 0;
+    bool all = true;
+    double worst = 0.0;
+    for (int i : rep_idx) {
+      const bool cplx = kept[i].im != 0.0;
+      R* xr = X.p + (size_t)slot * n;
+      R* xi = cplx ? X.p + (size_t)(slot + 1) * n : nullptr;
+      FV_TRY(combine(Ycols[first_col[i]], xr));
+      if (cplx) FV_TRY(combine(Ycols[first_col[i] + 1], xi));
+      double rr, ii = 0.0, rAr, iAi = 0.0, rAi = 0.0, iAr = 0.0;
+      FV_TRY(A.apply(xr, w.p));
+      FV_TRY(V.dot(xr, xr, &rr));
+      FV_TRY(V.dot(xr, w.p, &rAr));
+      if (cplx) {
+        FV_TRY(A.apply(xi, y1.p));
+        FV_TRY(V.dot(xi, xi, &ii));
+        FV_TRY(V.dot(xi, y1.p, &iAi));
+        FV_TRY(V.dot(xr, y1.p, &rAi));
+        FV_TRY(V.dot(xi, w.p, &iAr));
+      }
+      // x = xr + i xi: x^H A x = rAr + iAi + i (rAi - iAr)
+      const double xn2 = rr + ii;
+      double lr = (rAr + iAi) / xn2, li = cplx ? (rAi - iAr) / xn2 : 0.0;
+      if (cplx && li < 0.0) {  // the +Im member of the pair is reported first
+        li = -li;
+        FV_TRY(V.lin(xi, {{-1.0, xi}}));
+        FV_TRY(V.lin(y1.p, {{-1.0, y1.p}}));
+      }
+      double res2, t;
+      if (cplx) {  // A xr - (lr xr - li xi), A xi - (lr xi + li xr)
+        FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}, {li, xi}}));
+        FV_TRY(V.dot(w.p, w.p, &res2));
+        FV_TRY(V.lin(y1.p, {{1.0, y1.p}, {-lr, xi}, {-li, xr}}));
+        FV_TRY(V.dot(y1.p, y1.p, &t));
+        res2 += t;
+      } else {
+        FV_TRY(V.lin(w.p, {{1.0, w.p}, {-lr, xr}}));
+        FV_TRY(V.dot(w.p, w.p, &res2));
+      }
+      const double xn = std::sqrt(xn2), lam = std::hypot(lr, li);
+      const double rel = std::sqrt(res2) / (std::max(lam, 1e-300) * std::max(xn, 1e-300));
+      pairs.push_back({lr, li, rel, xn, slot});
+      if (!(rel <= o.tol)) all = false;
+      worst = std::max(worst, rel);
+      slot += cplx ? 2 : 1;
+    }
+    rep->restarts = restart;
+    if (worst <= 0.5 * best) {
+      best = worst;
+      best_at = restart;
+    }
+    const bool stalled = stall > 0 && restart - best_at >= stall;
+    worst_prev = worst;
+    if (all || mm < m || restart == o.max_restarts || stalled) {
+      status = all ? FV_OK : FV_ENOCONV;
+      // order by real part (then |Im|), +Im first; unit-norm vectors in that order into vecs_out
+      std::vector<int> po(pairs.size());
+      std::iota(po.begin(), po.end(), 0);
+      std::sort(po.begin(), po.end(), [&](int a, int b) {
+        if (pairs[a].lr != pairs[b].lr) return pairs[a].lr > pairs[b].lr;
+        return pairs[a].li > pairs[b].li;
+      });
+      int out = 0;
+      for (int pi : po) {
+        const Pair& pr = pairs[pi];
+        const int cnt = pr.li != 0.0 ? 2 : 1;
+        for (int c = 0; c < cnt && out < 64; ++c, ++out) {
+          re[out] = pr.lr;
+          im[out] = c == 0 ? pr.li : -pr.li;
+          rep->residual[out] = pr.res;
+          if (vecs_out) {
+            R* dst = (R*)vecs_out + (size_t)out * n;
+            FV_TRY(V.zero(dst));
+            FV_TRY(V.lin(dst, {{1.0 / std::max(pr.xn, 1e-300), X.p + (size_t)(pr.slot + c) * n}}));
+          }
+        }
+      }
+      nret = out;
+      FV_CUDA(cudaStreamSynchronize(g->stream));
+      break;
+    }
+    // ---- thick restart: orthonormalise the kept eigenvector columns Y (coefficient space, MGS twice)
+    std::vector<std::vector<double>> Qy;
+    for (const auto& y : Ycols) {
+      std::vector<double> v = y;
+      const double n0 = std::sqrt(std::inner_product(v.begin(), v.end(), v.begin(), 0.0));
+      for (int pass = 0; pass < 2; ++pass)
+        for (const auto& u : Qy) {
+          const double d = std::inner_product(u.begin(), u.end(), v.begin(), 0.0);
+          for (int t = 0; t < mm; ++t) v[t] -= d * u[t];
+        }
+      const double nv = std::sqrt(std::inner_product(v.begin(), v.end(), v.begin(), 0.0));
+      if (!(nv > 1e-10 * n0)) continue;
+      for (double& e : v) e /= nv;
+      Qy.push_back(v);
+    }
+    const int pn = (int)Qy.size();
+    if (pn == 0 || pn >= m) {  // nothing to keep: a fresh start from the leading reported Ritz vector
+      FV_TRY(V.copy(y0.p, X.p));
+      x = y0.p;
+      p = 0;
+      continue;
+    }
+    // new leading vectors V Q_y (into X, free by now, then into Vb), v_m moved to position p
+    for (int c = 0; c < pn; ++c) FV_TRY(combine(Qy[c], X.p + (size_t)c * n));
+    FV_TRY(V.copy(Vb.p + (size_t)pn * n, Vb.p + (size_t)mm * n));
+    for (int c = 0; c < pn; ++c) FV_TRY(V.copy(Vb.p + (size_t)c * n, X.p + (size_t)c * n));
+    // projected matrix: Q_y^T G Q_y, and the row g^T Q_y of v_m (g = G[mm][.], nonzero at mm-1 only)
+    std::vector<double> GQ((size_t)mm * pn, 0.0);
+    for (int r = 0; r < mm; ++r)
+      for (int c = 0; c < pn; ++c) {
+        double acc = 0.0;
+        for (int t = 0; t < mm; ++t) acc += Gm[(size_t)r * mm + t] * Qy[c][t];
+        GQ[(size_t)r * pn + c] = acc;
+      }
+    const double gmm = Gb[(size_t)mm * m + (mm - 1)];
+    std::fill(Gb.begin(), Gb.end(), 0.0);
+    for (int r = 0; r < pn; ++r)
+      for (int c = 0; c < pn; ++c) {
+        double acc = 0.0;
+        for (int t = 0; t < mm; ++t) acc += Qy[r][t] * GQ[(size_t)t * pn + c];
+        Gb[(size_t)r * m + c] = acc;
+      }
+    for (int c = 0; c < pn; ++c) Gb[(size_t)pn * m + c] = gmm * Qy[c][mm - 1];
+    p = pn;
+  }
+  rep->matvecs = mv + (refined ? refine->mv32 : 0);
+  rep->matvecs_fp64 = mixed ? 0 : mv;
+  rep->solves = sstats.solves;
+  rep->solves_short = sstats.short_;
+  rep->solve_worst = sstats.worst;
+  rep->nconv = nret;
+  rep->status = status;
+  for (int i = 0; i < nret && i < 64; ++i) {
+    const double sc = Gr > 0.0 ? 1.0 / std::sqrt(Gr) : 0.0;
+    rep->lam_scaled_re[i] = re[i] * sc;
+    rep->lam_scaled_im[i] = im[i] * sc;
+  }
+  rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return status;
+}
+
 template <typename R>
 static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
                         double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start = nullptr,
-                        ArnoldiCarry* carry = nullptr, int stall = 0) {
+                        ArnoldiCarry* carry = nullptr, int stall = 0, EulerRefine* refine = nullptr) {
+  if (o.euler_dt > 0.0) return arnoldi_si<R>(g, k, Gr, q64, o, re, im, vecs_out, rep, start, stall, refine);
   const auto t_start = std::chrono::steady_clock::now();
   const size_t n = 4 * g->N;
   const int m = o.m;
@@ -1483,30 +1972,8 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
   // far end of the spectrum: Rayleigh quotient of a short power iteration (the Krylov spaces of B stop
   // showing it, and the Chebyshev polynomial grows fast outside its ellipse)
-  // implicit-Euler transform (euler_dt > 0): B = (I - dt P J)^-1 on the divergence-free subspace, applied as
-  // the solution y of (P J - I/dt) y = in (any scale: only the Krylov space matters, the Ritz values come
-  // from V^T A V) by BiCGstab(2) right-preconditioned with P (L - I/dt)^-1.  It maps the leading values to
-  // the largest |mu| = 1/|1 - dt lam| and the stiff, convection-dominated far spectrum towards 0, where a
-  // Chebyshev ellipse cannot separate them at high cell Peclet numbers.  Inexact solves only slow the
-  // convergence; the true residuals are taken with A itself.
-  const bool euler = o.euler_dt > 0.0;
-  DevBuf<R> ework, epre;
-  if (euler) {
-    FV_TRY(ework.alloc(7 * n));
-    FV_TRY(epre.alloc(n));
-  }
-  Operator<R> Ae{g, Gr, sigma, q, &mv};
-  Ae.pre = euler ? epre.p : nullptr;
-  Ae.s = euler ? 1.0 / o.euler_dt : 0.0;
-  const double etol = mixed ? 1e-3 : std::max(1e-12, 0.01 * o.tol);
-  auto apply_euler = [&](const R* in, R* out) -> int {
-    SolveInfo info;
-    FV_TRY(bicgstab2<R>(Ae, in, out, etol, 4000, ework.p, info));
-    FV_TRY(apply_precond<R>(g, out, epre.p, Ae.s));
-    return V.copy(out, epre.p);
-  };
   double lam_far = (carry && carry->lam_far != 0.0) ? carry->lam_far : 0.0;
-  if (lam_far == 0.0 && !euler) {
+  if (lam_far == 0.0) {
     R* z = y1.p;
     double zn2;
     FV_TRY(V.dot(x, x, &zn2));
@@ -1573,11 +2040,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     // ---- m Arnoldi steps (CGS2) on A (first cycle) or on B = p(A) from p(A) x: the restart vector's error
     // in the stiff directions would otherwise sit in v_1 alone, where no later Krylov vector of B (which
     // damps those directions) can cancel it, and every Ritz vector would inherit it
-    if (euler) {
-      FV_TRY(V.copy(Vb.p, x));
-      FV_TRY(apply_euler(Vb.p, w.p));
-      x = w.p;
-    } else if (filt.on) {
+    if (filt.on) {
       FV_TRY(V.copy(Vb.p, x));
       FV_TRY(apply_filter(Vb.p, w.p));
       x = w.p;
@@ -1589,9 +2052,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     int mm = m;
     for (int j = 0; j < m; ++j) {
       const R* vj = Vb.p + (size_t)j * n;
-      if (euler)
-        FV_TRY(apply_euler(vj, w.p));
-      else if (filt.on)
+      if (filt.on)
         FV_TRY(apply_filter(vj, w.p));
       else
         FV_TRY(A.apply(vj, w.p));
@@ -1619,7 +2080,7 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     }
     // ---- Rayleigh-Ritz matrix G = V^T A V (for a Krylov basis of A it is the Hessenberg matrix itself)
     G.assign((size_t)mm * mm, 0.0);
-    if (!filt.on && !euler) {
+    if (!filt.on) {
       for (int i = 0; i < mm; ++i)
         for (int j = 0; j < mm; ++j) G[(size_t)i * mm + j] = H[(size_t)i * m + j];
     } else {
@@ -1768,7 +2229,6 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     }
     // ---- next ellipse: wanted + guard Ritz values outside, the rest and the far end inside
     int nf = std::min(nw + o.guard, mm - 2);
-    if (euler) nf = 0;  // no filter to fit
     if (nf < mm && nf >= 1 && ritz[nf - 1].im > 0) ++nf;
     nf = std::max(nf, nw);
     std::vector<Ritz> wanted(ritz.begin(), ritz.begin() + nf), unwanted(ritz.begin() + nf, ritz.end());
@@ -1776,11 +2236,10 @@ static int arnoldi_impl(fv_grid_s* g, int k, double Gr, const double* q64, const
     for (auto& u : unwanted) left = std::min(left, u.re);
     unwanted.push_back({1.05 * left, 0.0});
     double d = 0, c2 = 0, rate = 0;
-    if (!euler) best_ellipse(wanted, unwanted, d, c2, rate);
+    best_ellipse(wanted, unwanted, d, c2, rate);
     int deg = o.max_degree;
     if (rate > 1.0) deg = (int)std::ceil(std::log(kFilterGain) / std::log(rate));
     deg = std::max(o.min_degree, std::min(o.max_degree, deg));
-    if (euler) deg = 0;
     if (restart < 256) rep->degrees[restart] = deg;
     double lam_ref = -1e300;
     for (auto& wv : wanted) lam_ref = std::max(lam_ref, wv.re);
@@ -1849,6 +2308,7 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   FV_TRY(V.zero(z64.p));
   for (int i = 0; i < r1.nconv; ++i) {
     FV_TRY(launch_convert(g, n, X32.p + (size_t)i * n, t64.p));
+    FV_TRY(project_inplace<double>(g, t64.p, 1, 0.0, nullptr, nullptr));
     double t2;
     FV_TRY(V.dot(t64.p, t64.p, &t2));
     if (t2 > 0.0) FV_TRY(V.lin(z64.p, {{1.0, z64.p}, {1.0 / std::sqrt(t2), t64.p}}));
@@ -1858,7 +2318,41 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   if (vecs_out) FV_TRY(X64.alloc((size_t)(k + 1) * n));
   fv_arnoldi_opts o2 = o;
   o2.precision = FV_FP64;
-  const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry);
+  // implicit-Euler transform: the FP64 cycles' shifted solves by iterative refinement around FP32 GMRES
+  EulerRefine ref;
+  DevBuf<float> q32, b32, x32, pre32, basis32, w32;
+  DevBuf<double> r64, u64;
+  const bool euler = o.euler_dt > 0.0;
+  if (euler) {
+    FV_TRY(q32.alloc(n));
+    FV_TRY(b32.alloc(n));
+    FV_TRY(x32.alloc(n));
+    FV_TRY(pre32.alloc(n));
+    FV_TRY(basis32.alloc((size_t)(o.inner_m + 1) * n));
+    FV_TRY(w32.alloc(n));
+    FV_TRY(r64.alloc(n));
+    FV_TRY(u64.alloc(n));
+    FV_TRY(launch_convert(g, n, q, q32.p));
+    ref.g = g;
+    ref.Gr = Gr;
+    ref.sigma = (o.sigma != 0.0) ? o.sigma : g->sigma_default;
+    ref.s = 1.0 / o.euler_dt;
+    ref.q32 = q32.p;
+    ref.q64 = q;
+    ref.b32 = b32.p;
+    ref.x32 = x32.p;
+    ref.pre32 = pre32.p;
+    ref.basis32 = basis32.p;
+    ref.w32 = w32.p;
+    ref.r64 = r64.p;
+    ref.t64 = u64.p;
+    ref.inner_m = o.inner_m;
+    ref.inner_max = o.inner_max;
+    ref.tol32 = 1e-3;
+    ref.tol64 = o.inner_tol > 0.0 ? o.inner_tol : 1e-9;
+  }
+  const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry, 0,
+                                      euler ? &ref : nullptr);
   if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
     for (int i = 0; i < r2.nconv; ++i)
       FV_TRY(launch_convert(g, n, X64.p + (size_t)i * n, (float*)vecs_out + (size_t)i * n));
@@ -1867,6 +2361,9 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   rep->matvecs_low = r1.matvecs;
   rep->restarts = r1.restarts + r2.restarts;
   rep->matvecs = r1.matvecs + r2.matvecs;
+  rep->solves = r1.solves + r2.solves;
+  rep->solves_short = r1.solves_short + r2.solves_short;
+  rep->solve_worst = std::max(r1.solve_worst, r2.solve_worst);
   for (int i = 0; i < 256; ++i) rep->degrees[i] = (i <= r1.restarts) ? r1.degrees[i] : r2.degrees[i - r1.restarts - 1];
   FV_CUDA(cudaStreamSynchronize(g->stream));
   rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1884,7 +2381,8 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
   else
     fv_arnoldi_default_opts(&o);
   if (k < 1 || o.m > 200 || k + o.guard + 2 > o.m || o.min_degree < 1 || o.max_degree < o.min_degree ||
-      o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)) || !(o.euler_dt >= 0.0))
+      o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)) || !(o.euler_dt >= 0.0) ||
+      (o.euler_dt > 0.0 && (o.inner_m < 1 || o.inner_m > 500 || o.inner_max < 2 || !(o.inner_tol >= 0.0))))
     return invalid("bad Arnoldi options (need 1 <= k <= 63, k + guard + 2 <= m <= 200)");
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   fv_arnoldi_report rep;

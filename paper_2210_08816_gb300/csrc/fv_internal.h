@@ -100,6 +100,7 @@ struct fv_grid_s {
   fv::FdmDev<double> cd64, fd64;
   fv::FdmDev<float> cd32, fd32;
   fv::Workspace ws;
+  long long wait_spins = -1;  // polls of a device-side wait before it gives up; < 0: the default
   double sigma_default;
   double min_width[3];
   mutable fv::Profiler prof;
@@ -120,6 +121,11 @@ struct fv_grid_s {
 };
 
 namespace fv {
+
+// Polls of an mbarrier wait in the library's kernels before it records FV_ETIMEOUT and gives up (at least
+// seconds on every GPU this library targets, far above any legitimate wait).
+constexpr long long kDefaultWaitSpins = 1LL << 22;
+inline long long wait_spins(const fv_grid_s* g) { return g->wait_spins < 0 ? kDefaultWaitSpins : g->wait_spins; }
 
 // ------------------------------------------------------------------ error reporting
 void set_error(const std::string& msg);
@@ -179,6 +185,10 @@ bool stencil_pair_eligible(const fv_grid_s* g, const float* q, const float* v);
 // nvec > 1: v and out hold nvec states one after another (4N elements each), all in one launch.
 int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float* q, const float* v, float* out,
                         int nvec = 1);
+
+// Trilinear transfer of an FP64 state from grid gc to grid gf in physical coordinates, with the wall values
+// of Eqs. 4-6 (kernels_prolong.cu); runs on gf's stream.  Not projected.
+int launch_prolong(const fv_grid_s* gc, const double* qc, const fv_grid_s* gf, double* qf);
 
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>

@@ -46,14 +46,16 @@ class fv_arnoldi_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("m", C.c_int), ("tol", C.c_double), ("max_restarts", C.c_int),
                 ("max_degree", C.c_int), ("min_degree", C.c_int), ("guard", C.c_int),
                 ("seed", C.c_ulonglong), ("sigma", C.c_double), ("low_tol", C.c_double),
-                ("low_max_restarts", C.c_int), ("euler_dt", C.c_double)]
+                ("low_max_restarts", C.c_int), ("euler_dt", C.c_double), ("inner_m", C.c_int),
+                ("inner_max", C.c_int), ("inner_tol", C.c_double)]
 
 
 class fv_arnoldi_report(C.Structure):
     _fields_ = [("status", C.c_int), ("nconv", C.c_int), ("restarts", C.c_int), ("matvecs", C.c_longlong),
                 ("residual", C.c_double * 64), ("lam_scaled_re", C.c_double * 64),
                 ("lam_scaled_im", C.c_double * 64), ("degrees", C.c_int * 256), ("seconds", C.c_double),
-                ("restarts_low", C.c_int), ("matvecs_low", C.c_longlong)]
+                ("restarts_low", C.c_int), ("matvecs_low", C.c_longlong), ("matvecs_fp64", C.c_longlong),
+                ("solves", C.c_int), ("solves_short", C.c_int), ("solve_worst", C.c_double)]
 
 
 _lib = None
@@ -72,6 +74,8 @@ def lib():
             "fv_grid_destroy": (i, [vp]),
             "fv_set_stream": (i, [vp, vp]),
             "fv_state_elems": (C.c_longlong, [vp]),
+            "fv_set_wait_limit": (i, [vp, C.c_longlong]),
+            "fv_sync": (i, [vp]),
             "fv_residual": (i, [vp, d, vp, vp]),
             "fv_jvp": (i, [vp, i, d, vp, vp, vp]),
             "fv_project": (i, [vp, i, vp, i, d, C.POINTER(i), C.POINTER(d)]),
@@ -83,6 +87,7 @@ def lib():
             "fv_axpby": (i, [vp, i, d, vp, d, vp]),
             "fv_convert": (i, [vp, i, vp, vp]),
             "fv_diffusion_solve": (i, [vp, i, vp, vp]),
+            "fv_transfer": (i, [vp, vp, vp, vp]),
             "fv_jvp_project_batch": (i, [vp, i, d, d, vp, i, vp, vp, i]),
             "fv_get_tuning": (i, [vp, C.POINTER(i), C.POINTER(i)]),
             "fv_batch_plan_create": (i, [i, C.POINTER(vp), i, C.POINTER(d), C.POINTER(d), C.POINTER(vp),
@@ -107,10 +112,11 @@ def lib():
     return _lib
 
 
-EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_residual", "fv_jvp",
+EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elems", "fv_set_wait_limit", "fv_sync",
+            "fv_residual", "fv_jvp",
             "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot",
             "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
-            "fv_get_tuning", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
+            "fv_get_tuning", "fv_transfer", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
             "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile",
             "fv_profile_read", "fv_strerror", "fv_last_error"]
 
@@ -183,6 +189,16 @@ def fv_grid_destroy(g: Grid):
 
 def fv_set_stream(g: Grid, stream):
     _check(lib().fv_set_stream(g.h, C.c_void_p(stream)), "fv_set_stream")
+
+
+def fv_set_wait_limit(g: Grid, spins: int):
+    """Polls of every device-side wait of the handle's kernels before it gives up (< 0: the default)."""
+    _check(lib().fv_set_wait_limit(g.h, int(spins)), "fv_set_wait_limit")
+
+
+def fv_sync(g: Grid) -> int:
+    """Synchronise the handle's stream; returns FV_OK or FV_ETIMEOUT (a device-side wait gave up)."""
+    return _check(lib().fv_sync(g.h), "fv_sync", ok=(FV_OK, FV_ETIMEOUT))
 
 
 def fv_residual(g: Grid, Gr, q, F):
@@ -278,6 +294,14 @@ def fv_diffusion_solve(g: Grid, prec, x, out):
     return out
 
 
+def fv_transfer(g_from: Grid, q_from, g_to: Grid, q_to):
+    """q_to = the FP64 state q_from of grid g_from interpolated onto grid g_to (then projected there)."""
+    import torch
+    _check(lib().fv_transfer(g_from.h, _ptr(q_from, torch.float64, g_from.n, "q_from"), g_to.h,
+                             _ptr(q_to, torch.float64, g_to.n, "q_to")), "fv_transfer")
+    return q_to
+
+
 def fv_jvp_project(g: Grid, prec, Gr, sigma, q, v, out):
     dt = g.dtype(prec)
     _check(lib().fv_jvp_project(g.h, prec, float(Gr), float(sigma), _ptr(q, dt, g.n, "q"), _ptr(v, dt, g.n, "v"),
@@ -317,14 +341,21 @@ def fv_dot(g: Grid, prec, a, b) -> float:
 
 
 def fv_dot_noalloc(prec, a, b, result, stream=None):
-    """<a, b> into the device FP64 tensor `result` (one element), with no allocation in the library."""
+    """<a, b> into the device FP64 tensor `result` (one element), with no allocation in the library.
+    a, b and result must sit on one device; the call runs with that device current (and, by default, on
+    its current stream)."""
     import torch
     dt = torch.float64 if prec == FV_FP64 else torch.float32
     n = a.numel()
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    _check(lib().fv_dot_noalloc(int(prec), n, _ptr(a, dt, n, "a"), _ptr(b, dt, n, "b"),
-                                _ptr(result, torch.float64, 1, "result"), C.c_void_p(stream)), "fv_dot_noalloc")
+    for name, t in (("b", b), ("result", result)):
+        if isinstance(t, torch.Tensor) and t.device != a.device:
+            raise FvError(FV_EINVAL, "fv_dot_noalloc", f"{name} is on {t.device}, a is on {a.device}")
+    pa = _ptr(a, dt, n, "a")
+    with torch.cuda.device(a.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(a.device).cuda_stream
+        _check(lib().fv_dot_noalloc(int(prec), n, pa, _ptr(b, dt, n, "b"), _ptr(result, torch.float64, 1, "result"),
+                                    C.c_void_p(stream)), "fv_dot_noalloc")
     return result
 
 

@@ -54,4 +54,35 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(fv.fv_grid_desc) == 3 * 4 + 4 + 3 * 8 + 2 * 8
     # precond, forcing, then the pseudo-time step (double)
     assert ctypes.sizeof(fv.fv_newton_opts) == 4 + 4 + 2 * 8 + 3 * 4 + 4 + 2 * 8 + 4 + 4 + 8
-    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8  # ..., euler_dt
+    # ..., euler_dt, inner_m, inner_max, inner_tol
+    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4 + 8
+    # ..., seconds, restarts_low (+4 padding), matvecs_low, matvecs_fp64, solves, solves_short, solve_worst
+    assert ctypes.sizeof(fv.fv_arnoldi_report) == (4 + 4 + 4 + 4 + 8 + 3 * 64 * 8 + 256 * 4 + 8 + 4 + 4 + 8 + 8
+                                                   + 4 + 4 + 8)
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every field offset of the binding's ctypes structs equals the C compiler's offsetof for the header."""
+    import shutil
+    import subprocess
+    from paper_2210_08816_gb300 import fv
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [fv.fv_grid_desc, fv.fv_newton_opts, fv.fv_newton_report, fv.fv_arnoldi_opts, fv.fv_arnoldi_report]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cube_fv.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)

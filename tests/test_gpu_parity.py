@@ -173,6 +173,58 @@ def test_full_size_256_fp32_fused_matches_oracle(fv):
     assert rel(got, ref) <= TOL32_PROJ
 
 
+@pytest.mark.parametrize("shape", [(256, 12, 10), (10, 256, 12), (12, 10, 256)])
+def test_fp64_paths_on_a_256_cell_axis(fv, shape):
+    """The plain FP64 form (the comparison form of the 256^3 workload) along an axis of 256 stretched cells,
+    Gr = 2e8: J.v and the projection each against the oracle at 1e-12 of their results; the fused
+    J.v + projection at 1e-12 of its input J.v.  P removes the hydrostatic part of Gr T_v e_z, so the fused
+    result can be far smaller than the J.v it projects, and the FP64 rounding of that J.v (relative 1e-16 of
+    its own size on both sides) is what the difference is measured against."""
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q, v = state(og, 12, sigma=30.0), vector(og, 13)
+    Gr = 2.0e8
+    P = Projector(og)
+    qd, vd = dev(q, torch.float64), dev(v, torch.float64)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_jvp(g, fv.FV_FP64, Gr, qd, vd, out)
+    jv_ref = D.jvp(og, Gr, q, v)
+    assert rel(host(out, og.shape), jv_ref) <= TOL64
+    t = vd.clone()
+    fv.fv_project(g, fv.FV_FP64, t)
+    assert rel(host(t, og.shape), P.api(v)) <= TOL64
+    qf, vf = D.from_api(og, q), D.from_api(og, v)
+    J = D.jvp_full(og, Gr, qf, vf)
+    for sigma in (0.0, -2.0e5):
+        Jin = [J[c] - sigma * vf[c] for c in range(4)]
+        ref = P.full(Jin)
+        ref = D.to_api(og, [ref[c] + sigma * vf[c] for c in range(4)])
+        scale = D.to_api(og, Jin)
+        fv.fv_jvp_project(g, fv.FV_FP64, Gr, sigma, qd, vd, out)
+        got = host(out, og.shape)
+        err = max(float(np.max(np.abs(got[c] - ref[c]))) / max(float(np.max(np.abs(scale[c]))),
+                                                                 float(np.max(np.abs(ref[c]))), 1e-300)
+                  for c in range(4))
+        assert err <= TOL64, sigma
+
+
+def test_full_size_256_fp64_fused_matches_oracle(fv):
+    """256^3 tanh-stretched, Gr = 2e8 in plain FP64: the fused J.v + projection of the comparison form
+    against the oracle at 1e-12, every element."""
+    shape, Gr = (256, 256, 256), 2.0e8
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = state(og, 100, sigma=50.0, project=False)
+    v = vector(og, 101)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_jvp_project(g, fv.FV_FP64, Gr, 0.0, dev(q, torch.float64), dev(v, torch.float64), out)
+    got = host(out, og.shape)
+    del out
+    ref = Projector(og).api(D.jvp(og, Gr, q, v))
+    assert rel(got, ref) <= TOL64
+    g.close()
+
+
 def test_errors_are_status_codes(fv):
     with pytest.raises(fv.FvError) as e:
         fv.Grid(1, 4, 4)
@@ -331,22 +383,32 @@ def test_block_path_tensorcore_autotuned(fv):
 
 def test_batch_plan_several_grids_one_graph(fv):
     """fv_batch_plan: three continuation points on grids of different sizes (one of them without the
-    block stencil) in one captured graph with concurrent branches give the per-vector results; a replay
+    block stencil) in one captured graph with concurrent branches give the per-vector results, and the
+    last vector of every problem matches the oracle within the fused-path FP32 bound; a replay
     reads the vectors' current contents; growing a handle's block buffers invalidates the plan."""
     probs = [((64, 64, 64), 3.0e7, 3), ((40, 36, 32), 7.4e7, 2), ((96, 32, 48), 2.5e8, 2)]
-    keep = []
+    keep, oracle_ref = [], []
     for k, (shape, Gr, nvec) in enumerate(probs):
         og = D.Grid(*shape, stretch=1.5, Pr=PR)
         g = fv.Grid(*shape, stretch=1.5, Pr=PR)
-        q = dev(state(og, 60 + k), torch.float32)
-        V = torch.cat([dev(vector(og, 70 + 10 * k + i), torch.float32) for i in range(nvec)])
+        qa = round32(state(og, 60 + k))
+        va = [round32(vector(og, 70 + 10 * k + i)) for i in range(nvec)]
+        q = dev(qa, torch.float32)
+        V = torch.cat([dev(v, torch.float32) for v in va])
         W = torch.empty_like(V)
         sigma = -100.0 * (k + 1)
         ref = torch.empty_like(V)
         for i in range(nvec):
             fv.fv_jvp_project(g, fv.FV_FP32, Gr, sigma, q, V[i * g.n:(i + 1) * g.n], ref[i * g.n:(i + 1) * g.n])
         keep.append((g, Gr, sigma, q, V, W, nvec, ref))
+        # the oracle's result for the last vector of this problem (FP32-rounded inputs, FP64 oracle)
+        qf, vf = D.from_api(og, qa), D.from_api(og, va[-1])
+        J = D.jvp_full(og, Gr, qf, vf)
+        r = Projector(og).full([J[c] - sigma * vf[c] for c in range(4)])
+        oracle_ref.append((og, D.to_api(og, [r[c] + sigma * vf[c] for c in range(4)])))
     plan = fv.BatchPlan([k[:7] for k in keep], fv.FV_FP32, autotune=True)
+    for (g, Gr, sigma, q, V, W, nvec, ref), (og, exp) in zip(keep, oracle_ref):
+        assert rel(host(W[(nvec - 1) * g.n:nvec * g.n], og.shape), exp) <= TOL32_PROJ, og.shape
 
     def check(scale):
         torch.cuda.synchronize()
@@ -374,3 +436,19 @@ def test_batch_plan_several_grids_one_graph(fv):
     plan.close()
     for k in keep:
         k[0].close()
+
+
+@pytest.mark.parametrize("src,dst", [((20, 16, 12), (33, 27, 21)), ((64, 64, 64), (96, 80, 72)), ((33, 27, 21), (20, 16, 12))])
+def test_grid_transfer_matches_oracle(fv, src, dst):
+    """fv_transfer (grid sequencing) against the oracle's trilinear transfer and projection, FP64, 1e-12."""
+    from oracle import transfer as TR
+    oa, ob = D.Grid(*src, stretch=1.5, Pr=PR), D.Grid(*dst, stretch=1.5, Pr=PR)
+    ga, gb = fv.Grid(*src, stretch=1.5, Pr=PR), fv.Grid(*dst, stretch=1.5, Pr=PR)
+    qa = state(oa, 91, sigma=3.0)
+    ref = D.to_api(ob, TR.transfer(oa, D.from_api(oa, qa), ob))
+    out = torch.empty(gb.n, dtype=torch.float64, device="cuda")
+    fv.fv_transfer(ga, dev(qa, torch.float64), gb, out)
+    torch.cuda.synchronize()
+    assert rel(host(out, ob.shape), ref) <= TOL64
+    ga.close()
+    gb.close()

@@ -151,14 +151,14 @@ def test_arnoldi_32cube_matches_stored_oracle_eigenvalues(fv, cube32):
 def test_arnoldi_euler_transform_32cube_matches_stored_oracle_eigenvalues(fv, cube32):
     """Arnoldi on the implicit-Euler propagator (I - dt P J)^-1 instead of the Chebyshev polynomial:
     the same four leading eigenvalues of the 32^3, Gr = 1e5 workload as the oracle's stored ones (FP64
-    to 1e-8; the mixed form to 1e-6)."""
+    to 1e-8; the mixed form, whose FP64 cycles solve by iterative refinement around FP32 GMRES, to 1e-6)."""
     og, g, Gr, q, st, rep = cube32
     assert st == fv.FV_OK
     ref = _golden_eigs("config0_eigs_32.txt")
     o = fv.fv_arnoldi_default_opts()
     o.tol = 1e-9
     o.euler_dt = 0.01
-    o.max_restarts = 20
+    o.max_restarts = 8
     st, lam, r64 = fv.arnoldi_leading(g, 4, Gr, q, o)
     assert st == fv.FV_OK, (lam, list(r64.residual[:4]))
     assert len(lam) == len(ref) and np.allclose(np.array(lam), ref, rtol=1e-8, atol=0), (lam, ref)
@@ -245,3 +245,47 @@ def test_newton_pseudo_transient_from_conduction(fv):
     r = P.full(D.residual_full(og, Gr, D.from_api(og, res["ptc"])))
     scale = max(float(np.max(np.abs(a))) for a in D.residual_full(og, Gr, D.conduction_state(og)))
     assert max(float(np.max(np.abs(a))) for a in r) <= 1e-9 * scale
+
+
+@pytest.fixture(scope="module")
+def cube16_high_gr(fv):
+    """16^3 tanh-stretched (s = 1.5), Gr = 1.6e6: GPU Newton by pseudo-transient continuation from conduction."""
+    shape, Gr = (16, 16, 16), 1.6e6
+    og = D.Grid(*shape, stretch=1.5, Pr=PR)
+    g = fv.Grid(*shape, stretch=1.5, Pr=PR)
+    q = dev(conduction_api(og))
+    o = fv.fv_newton_default_opts()
+    o.tol = 1e-12
+    o.max_newton = 60
+    o.ptc_dt0 = 1e-3
+    o.gr_start, o.gr_ratio = 1e5, 4.0
+    st, rep = fv.newton_steady(g, Gr, q, o)
+    return og, g, Gr, q, st, rep
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_shift_invert_arnoldi_matches_independent_oracle_at_high_gr(fv, cube16_high_gr, prec_name):
+    """The implicit-Euler (shift-invert) Arnoldi with thick restarts against eigenvalues that the oracle
+    computed by a different method: Newton with sparse-LU corrections and ARPACK shift-invert on the saddle
+    pencil at several shifts along the imaginary axis (tests/golden/make_high_gr_eigs.py).  The six leading
+    values include a pair with |Im| ~ 820, far from the real shift: it is found because dt |Im| stays small.
+    FP64 to 1e-8, the mixed form to 1e-6; the GPU steady state is certified by the oracle's residual."""
+    og, g, Gr, q, st, rep = cube16_high_gr
+    assert st == fv.FV_OK, list(rep.history[:rep.newton_steps + 1])
+    got = host(q, og.shape)
+    P = Projector(og)
+    r = P.full(D.residual_full(og, Gr, D.from_api(og, got)))
+    assert max(float(np.max(np.abs(a))) for a in r) <= 1e-8 * rep.residual0
+    ref = _golden_eigs("eigs_16_stretched_gr1.6e6.txt")[:6]
+    o = fv.fv_arnoldi_default_opts()
+    o.euler_dt = 3e-4
+    o.m = 30
+    o.max_restarts = 12
+    o.inner_m = 60
+    o.tol = 1e-9 if prec_name == "fp64" else 1e-6
+    o.precision = fv.FV_FP64 if prec_name == "fp64" else fv.FV_FP32
+    st, lam, r64 = fv.arnoldi_leading(g, 6, Gr, q, o)
+    assert st == fv.FV_OK, (lam, list(r64.residual[:r64.nconv]))
+    lam = np.array(lam[:6])
+    rtol = 1e-8 if prec_name == "fp64" else 1e-6
+    assert np.allclose(lam, ref, rtol=rtol, atol=0), (lam, ref)
