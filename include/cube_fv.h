@@ -230,6 +230,25 @@ int fv_diffusion_solve(fv_grid g, int prec, const void* in, void* out);
  * Both handles must belong to the current device.  Errors: FV_EINVAL, FV_ECUDA, FV_ENOMEM. */
 int fv_transfer(fv_grid from, const double* q_from, fv_grid to, double* q_to);
 
+/* Diagnostics of Section 4.2.3 for an FP64 state q (device double[4N]): ekin (host, may be NULL) gets
+ * the total kinetic energy of Eq. 12, 1/2 sum of u_f^2 over the faces of every velocity component, each
+ * weighted by its staggered control volume (centre spacing along its own axis times the cell widths
+ * across); nu (host, may be NULL) the Nusselt number of Eq. 13 as printed, the sum over the hot wall's
+ * cells of (T - 1) / (dx_0 / 2) dy dz (conduction gives -1).  Synchronises the handle's stream.
+ * Errors: FV_EINVAL, FV_ECUDA. */
+int fv_diagnostics(fv_grid g, const double* q, double* ekin, double* nu);
+
+/* Time-dependent calculation (Section 4.2.3 runs the full equations in time at slightly sub- and
+ * supercritical Gr and monitors E_kin and Nu): nsteps steps of size dt of the semi-implicit scheme
+ *     q_{n+1} = q_n + P (I - dt L)^-1 dt F(q_n; Gr),
+ * diffusion L backward in time (inverted directly, as fv_diffusion_solve does, with the shift 1/dt),
+ * convection and buoyancy forward, the velocity increment made divergence free by the projection P (the
+ * pressure correction).  First order in dt; stable for dt below the convective limit (cell size over
+ * velocity).  q (device double[4N]) is advanced in place.  ekin, nu: host double[nsteps + 1] or NULL,
+ * receive the diagnostics of fv_diagnostics before the first step and after every step.
+ * Errors: FV_EINVAL, FV_ENAN (diagnostics not finite: an unstable step), FV_ECUDA, FV_ENOMEM. */
+int fv_time_step(fv_grid g, double Gr, double dt, int nsteps, double* q, double* ekin, double* nu);
+
 /* Element-type conversion of a state: FP64 -> FP32 (to_fp32 = 1) or back. */
 int fv_convert(fv_grid g, int to_fp32, const void* src, void* dst);
 

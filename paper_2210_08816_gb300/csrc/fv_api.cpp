@@ -1060,6 +1060,51 @@ int fv_batch_plan_destroy(fv_batch_plan plan) {
   return FV_OK;
 }
 
+int fv_diagnostics(fv_grid g, const double* q, double* ekin, double* nu) {
+  if (!g || !q) return invalid("null argument");
+  FV_TRY(launch_ekin(g, q, 0));
+  FV_TRY(launch_nusselt(g, q, 1));
+  double v[2];
+  FV_TRY(read_scalars(g, 0, 2, v));
+  if (ekin) *ekin = v[0];
+  if (nu) *nu = v[1];
+  return FV_OK;
+}
+
+int fv_time_step(fv_grid g, double Gr, double dt, int nsteps, double* q, double* ekin, double* nu) {
+  if (!g || !q) return invalid("null argument");
+  if (!(dt > 0.0) || nsteps < 0) return invalid("need dt > 0 and nsteps >= 0");
+  FV_TRY(ensure_ws<double>(g));
+  const size_t n = 4 * g->N;
+  DevBuf<double> F;
+  FV_TRY(F.alloc(n));
+  Vec<double> V{g, n};
+  auto record = [&](int i) -> int {
+    if (!ekin && !nu) return FV_OK;
+    FV_TRY(launch_ekin(g, q, 0));
+    FV_TRY(launch_nusselt(g, q, 1));
+    double v[2];
+    FV_TRY(read_scalars(g, 0, 2, v));
+    if (ekin) ekin[i] = v[0];
+    if (nu) nu[i] = v[1];
+    if (!std::isfinite(v[0]) || !std::isfinite(v[1])) {
+      set_error("non-finite diagnostics: the time step is unstable");
+      return FV_ENAN;
+    }
+    return FV_OK;
+  };
+  FV_TRY(record(0));
+  for (int it = 1; it <= nsteps; ++it) {
+    // delta = (I - dt L)^-1 dt F(q) = -(L - I/dt)^-1 F(q); its velocity projected; q += delta
+    FV_TRY(launch_residual<double>(g, Gr, q, F.p));
+    FV_TRY(diffusion_solve<double>(g, F.p, F.p, 1.0 / dt));
+    FV_TRY(project_inplace<double>(g, F.p, 1, 0.0, nullptr, nullptr));
+    FV_TRY(V.lin(q, {{1.0, q}, {-1.0, F.p}}));
+    FV_TRY(record(it));
+  }
+  return FV_OK;
+}
+
 int fv_transfer(fv_grid from, const double* q_from, fv_grid to, double* q_to) {
   if (!from || !to || !q_from || !q_to) return invalid("null argument");
   if ((const void*)q_from == (const void*)q_to) return invalid("q_to must not alias q_from");
@@ -1580,7 +1625,9 @@ static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const f
   const double s = 1.0 / o.euler_dt;
   const bool refined = refine != nullptr && std::is_same<R, double>::value;
   // Ritz values kept over a restart (largest |mu|) and reported (the k of largest real part among them)
-  const int keep_max = std::max(1, std::min(m - 2, std::max(k + o.guard, 2 * k)));
+  // (a Ritz value of modest |mu| but large real part, e.g. a pair with a large imaginary part, is reported
+  // only if it is kept, hence three times k)
+  const int keep_max = std::max(1, std::min(m - 4, std::max(k + o.guard, 3 * k)));
   DevBuf<R> qR, Vb, w, y0, y1, X;
   if (mixed) {
     FV_TRY(qR.alloc(n));

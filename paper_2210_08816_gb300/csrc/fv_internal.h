@@ -190,6 +190,11 @@ int launch_stencil_pair(const fv_grid_s* g, double Gr, double sigma, const float
 // of Eqs. 4-6 (kernels_prolong.cu); runs on gf's stream.  Not projected.
 int launch_prolong(const fv_grid_s* gc, const double* qc, const fv_grid_s* gf, double* qf);
 
+// Diagnostics of Section 4.2.3 (kernels_diag.cu), FP64 state q: E_kin (Eq. 12) and the hot-wall Nusselt
+// number (Eq. 13) into g->ws.scalars[slot].
+int launch_ekin(const fv_grid_s* g, const double* q, int slot);
+int launch_nusselt(const fv_grid_s* g, const double* q, int slot);
+
 // Fast-diagonalisation Poisson solve (kernels_fdm.cu): phi = (DG)^+ rhs; rhs and phi may alias.
 template <typename R>
 int launch_poisson(const fv_grid_s* g, const R* rhs, R* phi, R* tmp);

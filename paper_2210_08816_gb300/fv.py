@@ -88,6 +88,8 @@ def lib():
             "fv_convert": (i, [vp, i, vp, vp]),
             "fv_diffusion_solve": (i, [vp, i, vp, vp]),
             "fv_transfer": (i, [vp, vp, vp, vp]),
+            "fv_diagnostics": (i, [vp, vp, C.POINTER(d), C.POINTER(d)]),
+            "fv_time_step": (i, [vp, d, d, i, vp, C.POINTER(d), C.POINTER(d)]),
             "fv_jvp_project_batch": (i, [vp, i, d, d, vp, i, vp, vp, i]),
             "fv_get_tuning": (i, [vp, C.POINTER(i), C.POINTER(i)]),
             "fv_batch_plan_create": (i, [i, C.POINTER(vp), i, C.POINTER(d), C.POINTER(d), C.POINTER(vp),
@@ -116,7 +118,7 @@ EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elem
             "fv_residual", "fv_jvp",
             "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot",
             "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
-            "fv_get_tuning", "fv_transfer", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
+            "fv_get_tuning", "fv_transfer", "fv_diagnostics", "fv_time_step", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
             "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile",
             "fv_profile_read", "fv_strerror", "fv_last_error"]
 
@@ -300,6 +302,25 @@ def fv_transfer(g_from: Grid, q_from, g_to: Grid, q_to):
     _check(lib().fv_transfer(g_from.h, _ptr(q_from, torch.float64, g_from.n, "q_from"), g_to.h,
                              _ptr(q_to, torch.float64, g_to.n, "q_to")), "fv_transfer")
     return q_to
+
+
+def fv_diagnostics(g: Grid, q):
+    """(E_kin, Nu) of the FP64 state q (Eqs. 12 and 13)."""
+    import torch
+    e, nu = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().fv_diagnostics(g.h, _ptr(q, torch.float64, g.n, "q"), C.byref(e), C.byref(nu)), "fv_diagnostics")
+    return e.value, nu.value
+
+
+def fv_time_step(g: Grid, Gr, dt, nsteps, q):
+    """Advance the FP64 state q in place by nsteps semi-implicit steps; returns the (E_kin, Nu) histories
+    (nsteps + 1 values each, before the first step and after every step)."""
+    import torch
+    e = (C.c_double * (nsteps + 1))()
+    nu = (C.c_double * (nsteps + 1))()
+    _check(lib().fv_time_step(g.h, float(Gr), float(dt), int(nsteps), _ptr(q, torch.float64, g.n, "q"), e, nu),
+           "fv_time_step")
+    return list(e), list(nu)
 
 
 def fv_jvp_project(g: Grid, prec, Gr, sigma, q, v, out):
