@@ -300,6 +300,10 @@ def gpu_arm(args, ws, rank, local):
     # (the norm is summed inside the correction pass)
     step_bytes = (12 + 4 + 12 + 17) * N * 4
     breakdown = {k: {"ms_per_step": round(v[0] / K, 4), "launches_per_step": v[1] / K} for k, v in prof.items()}
+    # the pressure solve's share of the step: the most that any replacement of the direct solve (a learned
+    # Poisson surrogate included) could remove, since the direct solve needs one pass (I_p = 1)
+    poisson_ms = (prof["transform_tc"][0] + prof["transform"][0]) / K
+    breakdown["poisson_solve_share"] = round(poisson_ms / ms_step, 4) if ms_step > 0 else None
 
     # e2e through the C-ABI with host buffers: H2D of the step's input vector, the step, D2H of the result
     e2e = None

@@ -384,6 +384,49 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o);
 int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, const fv_arnoldi_opts* opts,
                     double* re, double* im, void* vecs, fv_arnoldi_report* report);
 
+/* ---------------------------------------------------------------- critical Gr (Section 4.1, Table 1) */
+/* Which eigenvalue's real part the secant drives to zero. */
+enum { FV_MODE_LEADING = 0, FV_MODE_REAL = 1, FV_MODE_OSCILLATORY = 2 };
+
+typedef struct {
+    double gr_a, gr_b;    /* the first two Gr of the iteration (ideally bracketing the crossing) */
+    double tol;           /* stop when |Gr_{i+1} - Gr_i| <= tol Gr_i (default 1e-7) */
+    int max_iter;         /* steady-state + eigenvalue evaluations after the first two (default 16) */
+    int mode;             /* FV_MODE_LEADING: the largest real part among the k computed (the first of
+                             several modes to cross); FV_MODE_REAL: the largest among the real ones (a
+                             steady bifurcation); FV_MODE_OSCILLATORY: among the complex pairs (a Hopf
+                             bifurcation, whose Im gives the critical frequency) */
+} fv_critical_opts;
+
+typedef struct {
+    int status;           /* FV_OK, FV_ENOCONV (iteration cap, or an inner Newton / Arnoldi failure) */
+    int evaluations;
+    double gr_cr;         /* last iterate: Re lam(gr_cr) ~ 0 */
+    double lam_re, lam_im;/* the tracked eigenvalue at gr_cr (Form A units) */
+    double omega_scaled;  /* lam_im / sqrt(gr_cr): the angular frequency in the paper's time scale */
+    double gr[40], re[40], im[40];   /* every evaluation */
+} fv_critical_report;
+
+void fv_critical_default_opts(fv_critical_opts* o);
+
+/* Critical Grashof number of one grid (Section 4.1: the critical values on each grid are the input of
+ * the Richardson extrapolation of Table 1): the Gr at which the real part of the tracked eigenvalue of
+ * the linearised problem about the steady state crosses zero.  Each evaluation continues the steady
+ * state by newton_steady (newton options `nopts`, its continuation ladder ignored: the start is the
+ * state of the nearest Gr evaluated before) and computes k leading eigenvalues by arnoldi_leading
+ * (`aopts`).  The iteration is the secant method on Re lam(Gr), switched to the Illinois variant of the
+ * false-position method once a sign change brackets the crossing.  q_inout (device double[4N]): on entry
+ * a divergence-free start for Newton at gr_a (e.g. a steady state nearby or conduction); on return the
+ * steady state at gr_cr.  Errors: FV_EINVAL, FV_ENOCONV, FV_ENAN, FV_ECUDA, FV_ENOMEM. */
+int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton_opts* nopts, const fv_arnoldi_opts* aopts,
+                   const fv_critical_opts* copts, fv_critical_report* report);
+
+/* Richardson extrapolation to zero grid size (Section 4.1: the critical values depend linearly on the
+ * squared average grid size): the least-squares line value = limit + slope h2 through n >= 2 points
+ * (h2[i], value[i]) (host arrays), e.g. h2 = (nx ny nz)^(-2/3).  limit, slope: host, either may be NULL.
+ * Errors: FV_EINVAL (n < 2, or all h2 equal). */
+int fv_richardson(int n, const double* h2, const double* value, double* limit, double* slope);
+
 /* ---------------------------------------------------------------- measurement */
 /* Per-kernel-class timing with CUDA events recorded on the handle's stream around every launch.
  * fv_profile(g, 1) clears and starts recording, fv_profile(g, 0) stops.  fv_profile_read

@@ -131,11 +131,22 @@ def _constraint_blocks(grid: D.Grid):
     return Gfull, Dfull, npres
 
 
-def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30):
+def symmetrise(q):
+    """Mean of q over the symmetry group of Section 2 (identity, reflection y -> 1-y, rotation about
+    x = z = 1/2, centro-symmetry; T maps affinely).  The symmetric steady states are its fixed points."""
+    from .diagnostics import sym_2d, sym_3d, sym_ref
+    imgs = [q, sym_ref(q), sym_2d(q), sym_3d(q)]
+    return [sum(im[c] for im in imgs) / 4.0 for c in range(4)]
+
+
+def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30, atol=0.0, symmetric=False):
     """Steady state of Eqs. 1-6 by Newton's method with exact (sparse LU) corrections:
         [[J(q), -G], [D, 0]] [delta; p] = [-F(q); 0],   q <- q + delta.
     q0 (full arrays) must be divergence free; every delta is, so q stays so.  The residual is the
-    projected one, P F = F - G p with D (F - G p) = 0; stop when ||P F||_inf <= tol max(1, ||P F(q0)||_inf).
+    projected one, P F = F - G p with D (F - G p) = 0; stop when ||P F||_inf <= tol max(1, ||P F(q0)||_inf)
+    or ||P F||_inf <= atol (a start that is already a steady state cannot gain a factor tol on its
+    round-off level residual).  symmetric: every iterate is symmetrised (the branch of symmetric states,
+    on which a symmetry-breaking eigenvalue crossing zero leaves the Jacobian regular).
     Returns (q, report)."""
     q = [a.copy() for a in q0]
     n = D.n_unknowns(grid)
@@ -147,7 +158,7 @@ def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30):
         PF = proj.solve(np.concatenate([F, np.zeros(npres)]))[:n]
         rn = float(np.max(np.abs(PF)))
         hist.append(rn)
-        if rn <= tol * max(1.0, hist[0]):
+        if rn <= tol * max(1.0, hist[0]) or rn <= atol:
             return q, {"status": "converged", "residual": hist, "steps": it}
         if it == max_newton:
             break
@@ -165,7 +176,7 @@ def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30):
                 if rt < rn:
                     break
             lam *= 0.5
-        q = qt
+        q = symmetrise(qt) if symmetric else qt
     return q, {"status": "max_newton", "residual": hist, "steps": max_newton}
 
 

@@ -557,6 +557,7 @@ static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv
     return FV_OK;
   }
   std::vector<double> H((size_t)(m + 1) * m), h(m + 1), h2(m + 1), y;
+  double rel_cycle = 2.0;
   for (;;) {
     // r = b - A x into basis[0]
     FV_TRY(A.apply(x, w));
@@ -571,6 +572,13 @@ static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv
       return FV_OK;
     }
     if (info.matvecs >= max_mv) return FV_OK;
+    // a restart cycle that left the true residual nearly where it was: the solve sits at its round-off
+    // floor (FP32 data) or stagnates; stop rather than spend the product budget
+    if (info.rel > 0.9 * rel_cycle) {
+      info.stalled = true;
+      return FV_OK;
+    }
+    rel_cycle = info.rel;
     FV_TRY(V.lin(basis, {{1.0 / beta, basis}}));
     std::fill(H.begin(), H.end(), 0.0);
     int used = 0;
@@ -1545,13 +1553,15 @@ struct EulerRefine {
     double xn2;
     FV_TRY(V64.dot(in, in, &xn2));
     const double xn = std::sqrt(xn2);
-    double rel = 1.0;
+    double rel = 1.0, rel_prev = 2.0;
     for (int it = 0; it <= max_outer; ++it) {
       double rn2;
       FV_TRY(V64.dot(r64, r64, &rn2));
       const double rn = std::sqrt(rn2);
       rel = xn > 0.0 ? rn / xn : 0.0;
-      if (rel <= tol64 || it == max_outer) break;
+      // converged, or the FP32 corrections no longer halve the FP64 residual (its round-off floor)
+      if (rel <= tol64 || it == max_outer || rel > 0.5 * rel_prev) break;
+      rel_prev = rel;
       FV_TRY(V64.lin(t64, {{1.0 / rn, r64}}));
       FV_TRY(launch_convert(g, n, t64, b32));
       FV_TRY(V32.zero(x32));
@@ -1611,8 +1621,7 @@ constexpr double kFilterGain = 1e2;
 // |mu|, orthonormalised in coefficient space (Y = Q_y R, G Q_y = Q_y (Q_y^T G Q_y) because span Y is
 // G-invariant), give the new leading basis V_m Q_y with projected block Q_y^T G Q_y, followed by v_m with
 // the row g^T Q_y; the Arnoldi process then expands from v_m.  Inexact solves perturb this relation at
-// their tolerance, which is relaxed while the residuals are large (1e-3 of the previous cycle's largest,
-// within [floor, 1e-2]).
+// their tolerance; since the kept block is never recomputed, every solve runs to the same tolerance.
 template <typename R>
 static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const fv_arnoldi_opts& o, double* re,
                       double* im, void* vecs_out, fv_arnoldi_report* rep, const R* start, int stall,
@@ -1702,7 +1711,9 @@ static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const f
   int best_at = 0, p = 0, status = FV_ENOCONV, nret = 0;
   std::vector<double> Gm, Hg, Qg, hre, him, sh;
   for (int restart = 0; restart <= o.max_restarts; ++restart) {
-    etol = std::min(1e-2, std::max(etol_floor, 1e-3 * worst_prev));
+    // one accuracy for every solve: the projected matrix of the kept vectors is carried over restarts and
+    // never recomputed, so a loose early solve would cap the accuracy of every later cycle
+    etol = etol_floor;
     if (refined) refine->tol64 = etol;
     if (p == 0) {  // fresh start: v_0 = B x / ||B x||
       std::fill(Gb.begin(), Gb.end(), 0.0);
@@ -2443,4 +2454,185 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
   rep.status = st;
   if (report) *report = rep;
   return st;
+}
+
+// ====================================================================== critical Gr (Section 4.1)
+namespace fv {
+
+// The tracked eigenvalue among the returned ones: largest real part overall, among the real values, or
+// among the complex pairs (+Im member).  false if the mode has no representative.
+static bool pick_mode(int mode, int nconv, const double* re, const double* im, double* lr, double* li) {
+  bool found = false;
+  for (int i = 0; i < nconv; ++i) {
+    const bool cplx = im[i] != 0.0;
+    if (mode == FV_MODE_REAL && cplx) continue;
+    if (mode == FV_MODE_OSCILLATORY && (!cplx || im[i] < 0.0)) continue;
+    if (!found || re[i] > *lr) {
+      *lr = re[i];
+      *li = std::fabs(im[i]);
+      found = true;
+    }
+  }
+  return found;
+}
+
+}  // namespace fv
+
+extern "C" void fv_critical_default_opts(fv_critical_opts* o) {
+  if (!o) return;
+  o->gr_a = 0.0;
+  o->gr_b = 0.0;
+  o->tol = 1e-7;
+  o->max_iter = 16;
+  o->mode = FV_MODE_LEADING;
+}
+
+extern "C" int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton_opts* nopts,
+                              const fv_arnoldi_opts* aopts, const fv_critical_opts* copts, fv_critical_report* report) {
+  if (!g || !q_inout || !copts) return invalid("null argument");
+  const fv_critical_opts c = *copts;
+  if (!(c.gr_a > 0.0) || !(c.gr_b > 0.0) || c.gr_a == c.gr_b || !(c.tol > 0.0) || c.max_iter < 0 ||
+      c.max_iter > 38 || c.mode < FV_MODE_LEADING || c.mode > FV_MODE_OSCILLATORY || k < 1 || k > 62)
+    return invalid("bad critical-Gr options (need distinct gr_a, gr_b > 0, tol > 0, 0 <= max_iter <= 38)");
+  fv_newton_opts no;
+  if (nopts)
+    no = *nopts;
+  else
+    fv_newton_default_opts(&no);
+  no.gr_start = 0.0;  // every evaluation continues from the nearest state already computed
+  fv_arnoldi_opts ao;
+  if (aopts)
+    ao = *aopts;
+  else
+    fv_arnoldi_default_opts(&ao);
+  fv_critical_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  rep.status = FV_ENOCONV;
+  const size_t n = 4 * g->N;
+  // states of the evaluations so far: a Newton start for the next Gr is the one of the nearest Gr
+  std::vector<DevBuf<double>> states(c.max_iter + 2);
+  std::vector<double> grs;
+  std::vector<double> re(k + 1), im(k + 1);
+  Vec<double> V{g, n};
+  auto evaluate = [&](double gr, double* lr, double* li) -> int {
+    const int idx = (int)grs.size();
+    FV_TRY(states[idx].alloc(n));
+    if (idx == 0) {
+      FV_TRY(V.copy(states[idx].p, q_inout));
+    } else {
+      int near = 0;
+      for (int i = 1; i < idx; ++i)
+        if (std::fabs(std::log(grs[i] / gr)) < std::fabs(std::log(grs[near] / gr))) near = i;
+      FV_TRY(V.copy(states[idx].p, states[near].p));
+    }
+    fv_newton_report nr;
+    int st = newton_steady(g, gr, states[idx].p, &no, &nr);
+    if (st != FV_OK) {
+      set_error("critical Gr: Newton did not converge at Gr = " + std::to_string(gr));
+      return st == FV_ENOCONV ? FV_ENOCONV : st;
+    }
+    fv_arnoldi_report ar;
+    st = arnoldi_leading(g, k, gr, states[idx].p, &ao, re.data(), im.data(), nullptr, &ar);
+    if (st != FV_OK && st != FV_ENOCONV) return st;
+    if (!pick_mode(c.mode, ar.nconv, re.data(), im.data(), lr, li)) {
+      set_error("critical Gr: no eigenvalue of the tracked kind among the k computed at Gr = " +
+                std::to_string(gr) + " (raise k)");
+      return FV_ENOCONV;
+    }
+    grs.push_back(gr);
+    if (rep.evaluations < 40) {
+      rep.gr[rep.evaluations] = gr;
+      rep.re[rep.evaluations] = *lr;
+      rep.im[rep.evaluations] = *li;
+    }
+    ++rep.evaluations;
+    return FV_OK;
+  };
+  double fa, ia, fb, ib;
+  double a = c.gr_a, b = c.gr_b;
+  int st = evaluate(a, &fa, &ia);
+  if (st == FV_OK) st = evaluate(b, &fb, &ib);
+  int side = 0;  // Illinois: which end was kept last time (-1: a, +1: b)
+  bool bracketed = st == FV_OK && fa * fb <= 0.0;
+  double x = b, fx = fb, ix = ib;
+  for (int it = 0; st == FV_OK && it < c.max_iter; ++it) {
+    if (fb == fa) break;
+    double xn = b - fb * (b - a) / (fb - fa);
+    if (!bracketed) {  // secant: keep the step within twice the current spacing
+      const double lim = 2.0 * std::fabs(b - a);
+      xn = std::min(std::max(xn, b - lim), b + lim);
+    }
+    if (!(xn > 0.0)) xn = 0.5 * std::min(a, b);
+    double fn, in;
+    st = evaluate(xn, &fn, &in);
+    if (st != FV_OK) break;
+    x = xn;
+    fx = fn;
+    ix = in;
+    const bool done = std::fabs(xn - b) <= c.tol * std::fabs(b) || fn == 0.0;
+    // b is always the newest point; once a sign change is seen, a and b keep opposite signs
+    if (!bracketed && fn * fa < 0.0 && fn * fb > 0.0) {
+      bracketed = true;  // the crossing lies between a and xn: keep a
+      b = xn;
+      fb = fn;
+    } else if (!bracketed && fn * fb < 0.0) {
+      bracketed = true;  // between b and xn
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+      side = 0;
+    } else if (!bracketed) {  // secant step
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+    } else if (fn * fb < 0.0) {  // false position: the newest end changed sign, the old b becomes a
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+      side = 0;
+    } else {  // a is retained again: Illinois halves its value so that it is not retained forever
+      if (side == -1) fa *= 0.5;
+      side = -1;
+      b = xn;
+      fb = fn;
+    }
+    if (done) {
+      rep.status = FV_OK;
+      break;
+    }
+  }
+  if (rep.evaluations > 0) {
+    rep.gr_cr = x;
+    rep.lam_re = fx;
+    rep.lam_im = ix;
+    rep.omega_scaled = ix / std::sqrt(x);
+    // the steady state of the last evaluation
+    FV_CUDA(cudaMemcpyAsync(q_inout, states[grs.size() - 1].p, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                            g->stream));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  if (st != FV_OK) rep.status = st;
+  if (report) *report = rep;
+  return rep.status;
+}
+
+extern "C" int fv_richardson(int n, const double* h2, const double* value, double* limit, double* slope) {
+  if (n < 2 || !h2 || !value) return invalid("need n >= 2 points");
+  double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+  for (int i = 0; i < n; ++i) {
+    sx += h2[i];
+    sy += value[i];
+    sxx += h2[i] * h2[i];
+    sxy += h2[i] * value[i];
+  }
+  const double det = n * sxx - sx * sx;
+  if (!(std::fabs(det) > 1e-300)) return invalid("the grid sizes must differ");
+  const double b = (n * sxy - sx * sy) / det;
+  const double a = (sy - b * sx) / n;
+  if (limit) *limit = a;
+  if (slope) *slope = b;
+  return FV_OK;
 }

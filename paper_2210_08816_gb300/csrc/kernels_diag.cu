@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_ekin_partial(Geo<double> g, const 
     for (int d = 0; d < 3; ++d)
       if (d != c) inv *= g.idx[d][p[d]];
     const double u = q[t];
-    acc += u * u / inv;
+    acc += 0.5 * u * u / inv;
   }
   const double r = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = r;

@@ -58,6 +58,19 @@ class fv_arnoldi_report(C.Structure):
                 ("solves", C.c_int), ("solves_short", C.c_int), ("solve_worst", C.c_double)]
 
 
+class fv_critical_opts(C.Structure):
+    _fields_ = [("gr_a", C.c_double), ("gr_b", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("mode", C.c_int)]
+
+
+class fv_critical_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("evaluations", C.c_int), ("gr_cr", C.c_double), ("lam_re", C.c_double),
+                ("lam_im", C.c_double), ("omega_scaled", C.c_double), ("gr", C.c_double * 40),
+                ("re", C.c_double * 40), ("im", C.c_double * 40)]
+
+
+FV_MODE_LEADING, FV_MODE_REAL, FV_MODE_OSCILLATORY = 0, 1, 2
+
 _lib = None
 
 
@@ -101,6 +114,10 @@ def lib():
             "fv_arnoldi_default_opts": (None, [C.POINTER(fv_arnoldi_opts)]),
             "arnoldi_leading": (i, [vp, i, d, vp, C.POINTER(fv_arnoldi_opts), C.POINTER(d), C.POINTER(d), vp,
                                     C.POINTER(fv_arnoldi_report)]),
+            "fv_critical_default_opts": (None, [C.POINTER(fv_critical_opts)]),
+            "fv_critical_gr": (i, [vp, i, vp, C.POINTER(fv_newton_opts), C.POINTER(fv_arnoldi_opts),
+                                   C.POINTER(fv_critical_opts), C.POINTER(fv_critical_report)]),
+            "fv_richardson": (i, [i, C.POINTER(d), C.POINTER(d), C.POINTER(d), C.POINTER(d)]),
             "fv_profile": (i, [vp, i]),
             "fv_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong)]),
             "fv_strerror": (C.c_char_p, [i]),
@@ -119,7 +136,7 @@ EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elem
             "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot",
             "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
             "fv_get_tuning", "fv_transfer", "fv_diagnostics", "fv_time_step", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
-            "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_profile",
+            "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_critical_default_opts", "fv_critical_gr", "fv_richardson", "fv_profile",
             "fv_profile_read", "fv_strerror", "fv_last_error"]
 
 FV_PROF_CLASSES = 7
@@ -445,3 +462,30 @@ def arnoldi_leading(g: Grid, k, Gr, q, opts: fv_arnoldi_opts | None = None, vecs
     _check(st, "arnoldi_leading", ok=(FV_OK, FV_ENOCONV))
     lam = [complex(re[i], im[i]) for i in range(rep.nconv)]
     return st, lam, rep
+
+
+def fv_critical_default_opts() -> fv_critical_opts:
+    o = fv_critical_opts()
+    lib().fv_critical_default_opts(C.byref(o))
+    return o
+
+
+def fv_critical_gr(g: Grid, k, q, copts: fv_critical_opts, nopts: fv_newton_opts | None = None,
+                   aopts: fv_arnoldi_opts | None = None):
+    """Returns (status, report); q (FP64, in place) ends as the steady state at the critical Gr."""
+    import torch
+    rep = fv_critical_report()
+    st = lib().fv_critical_gr(g.h, int(k), _ptr(q, torch.float64, g.n, "q"), C.byref(nopts) if nopts else None,
+                              C.byref(aopts) if aopts else None, C.byref(copts), C.byref(rep))
+    _check(st, "fv_critical_gr", ok=(FV_OK, FV_ENOCONV))
+    return st, rep
+
+
+def fv_richardson(h2, values):
+    """(limit, slope) of the least-squares line values = limit + slope h2 (Richardson extrapolation)."""
+    n = len(h2)
+    a = (C.c_double * n)(*[float(x) for x in h2])
+    b = (C.c_double * n)(*[float(x) for x in values])
+    lim, sl = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().fv_richardson(n, a, b, C.byref(lim), C.byref(sl)), "fv_richardson")
+    return lim.value, sl.value

@@ -69,7 +69,8 @@ def test_struct_offsets_match_the_c_compiler(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [fv.fv_grid_desc, fv.fv_newton_opts, fv.fv_newton_report, fv.fv_arnoldi_opts, fv.fv_arnoldi_report]
+    structs = [fv.fv_grid_desc, fv.fv_newton_opts, fv.fv_newton_report, fv.fv_arnoldi_opts, fv.fv_arnoldi_report,
+               fv.fv_critical_opts, fv.fv_critical_report]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cube_fv.h"', "int main(void) {"]
     for st in structs:
         lines.append(f'printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
@@ -86,3 +87,18 @@ def test_struct_offsets_match_the_c_compiler(tmp_path):
         assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
         for name, _ in st._fields_:
             assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
+
+
+def test_richardson_extrapolation_is_the_least_squares_line(libpath):
+    """fv_richardson (host arithmetic, no GPU): exact for values linear in h^2, least squares otherwise."""
+    import numpy as np
+    from paper_2210_08816_gb300 import fv
+    h2 = [1 / 100.0 ** 2, 1 / 128.0 ** 2, 1 / 256.0 ** 2]
+    lim, sl = fv.fv_richardson(h2, [4.5e7 + 3e10 * x for x in h2])
+    assert lim == pytest.approx(4.5e7, rel=1e-13) and sl == pytest.approx(3e10, rel=1e-10)
+    vals = [4.61e7, 4.57e7, 4.52e7]
+    ref = np.polyfit(h2, vals, 1)
+    lim, sl = fv.fv_richardson(h2, vals)
+    assert lim == pytest.approx(ref[1], rel=1e-12) and sl == pytest.approx(ref[0], rel=1e-9)
+    with pytest.raises(fv.FvError):
+        fv.fv_richardson([1.0], [2.0])

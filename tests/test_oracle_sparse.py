@@ -81,3 +81,19 @@ def test_shift_invert_gr0_closed_form():
     # the leading values at Gr = 0 are the temperature block's (the Stokes block lies further left here)
     assert np.allclose(lam[:4].real, temp[:4], rtol=1e-11, atol=0)
     assert np.all(np.abs(lam[:4].imag) <= 1e-9 * np.abs(lam[:4].real))
+
+
+def test_symmetrise_projects_onto_the_symmetric_states():
+    """oracle.sparse.symmetrise: its result has all three symmetry measures (Eqs. 7-9) at round-off and the
+    velocity maps of Section 2 leave it unchanged; a symmetric steady state is a fixed point."""
+    g = D.Grid(8, 7, 6, stretch=1.5, Pr=PR)
+    q = _random_state(g, 9)
+    qs = S.symmetrise(q)
+    assert max(DG.symmetry_measures(g, qs[3])) <= 1e-14
+    for img in (DG.sym_ref(qs), DG.sym_2d(qs), DG.sym_3d(qs)):
+        for c in range(4):
+            assert np.max(np.abs(img[c] - qs[c])) <= 1e-14
+    qn, _ = S.newton_direct(g, 1.2e4, D.conduction_state(g), tol=1e-12)
+    qq = S.symmetrise(qn)
+    scale = max(float(np.max(np.abs(a))) for a in qn)
+    assert max(float(np.max(np.abs(qq[c] - qn[c]))) for c in range(4)) <= 1e-10 * scale   # Section 2: ~1e-9
