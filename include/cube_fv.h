@@ -340,11 +340,16 @@ typedef struct {
                              Chebyshev-preconditioned form of Section 1 */
     int inner_m;          /* euler_dt > 0: restart length of the GMRES shifted solves (default 50) */
     int inner_max;        /* euler_dt > 0: J.v + projections per shifted solve (default 3000) */
-    double inner_tol;     /* euler_dt > 0: relative residual of each shifted solve; 0 (default): 1e-9
-                             for FP64 solves, 1e-3 for FP32 ones (about their round-off floor).  In
-                             the FP64 cycles of the mixed form every shifted solve is FP64-accurate
-                             by iterative refinement: FP64 residual x - (I - dt P J) y, FP32 GMRES
-                             correction to 1e-3, until the FP64 residual is below inner_tol */
+    double inner_tol;     /* euler_dt > 0: relative residual of each shifted solve (every solve runs to
+                             it); 0 (default): max(1e-12, tol / 100) for FP64 solves, 1e-3 for FP32
+                             ones (about their round-off floor).  In the FP64 cycles of the mixed form
+                             every shifted solve is FP64-accurate by iterative refinement: FP64
+                             residual x - (I - dt P J) y, FP32 GMRES correction to 1e-3, until the FP64
+                             residual is below inner_tol or stops halving */
+    int vecs_fp64;        /* 1: `vecs` holds FP64 vectors whatever the precision (the mixed form's FP64
+                             cycles keep them in FP64; an FP32 copy would carry round-off of relative
+                             size u32 ||A|| / |lam| into a residual check).  0 (default): the element
+                             type of the precision */
 } fv_arnoldi_opts;
 
 typedef struct {

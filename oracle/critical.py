@@ -32,7 +32,7 @@ def critical_gr(grid: D.Grid, gr_lo: float, gr_hi: float, q_lo, mode: str, shift
     hist = []
 
     def f(gr, q):
-        q, rep = S.newton_direct(grid, gr, q, tol=1e-10, max_newton=25, atol=1e-6, symmetric=True)
+        q, rep = S.newton_direct(grid, gr, q, tol=1e-10, max_newton=25, atol=1e-5, symmetric=True)
         if rep["status"] != "converged":
             raise RuntimeError(f"Newton did not converge at Gr = {gr}")
         lam = tracked(S.shift_invert_eigs(grid, gr, q, shifts, k=k), mode)

@@ -1232,6 +1232,7 @@ void fv_arnoldi_default_opts(fv_arnoldi_opts* o) {
   o->inner_m = 50;
   o->inner_max = 3000;
   o->inner_tol = 0.0;
+  o->vecs_fp64 = 0;
 }
 
 }  // extern "C"
@@ -2411,9 +2412,13 @@ static int arnoldi_mixed(fv_grid_s* g, int k, double Gr, const double* q, const 
   }
   const int st = arnoldi_impl<double>(g, k, Gr, q, o2, re, im, vecs_out ? X64.p : nullptr, &r2, z64.p, &carry, 0,
                                       euler ? &ref : nullptr);
-  if (vecs_out && (st == FV_OK || st == FV_ENOCONV))
-    for (int i = 0; i < r2.nconv; ++i)
-      FV_TRY(launch_convert(g, n, X64.p + (size_t)i * n, (float*)vecs_out + (size_t)i * n));
+  if (vecs_out && (st == FV_OK || st == FV_ENOCONV)) {
+    if (o.vecs_fp64)
+      FV_CUDA(cudaMemcpyAsync(vecs_out, X64.p, sizeof(double) * n * r2.nconv, cudaMemcpyDeviceToDevice, g->stream));
+    else
+      for (int i = 0; i < r2.nconv; ++i)
+        FV_TRY(launch_convert(g, n, X64.p + (size_t)i * n, (float*)vecs_out + (size_t)i * n));
+  }
   *rep = r2;
   rep->restarts_low = r1.restarts;
   rep->matvecs_low = r1.matvecs;
@@ -2440,7 +2445,8 @@ extern "C" int arnoldi_leading(fv_grid g, int k, double Gr, const double* q, con
     fv_arnoldi_default_opts(&o);
   if (k < 1 || o.m > 200 || k + o.guard + 2 > o.m || o.min_degree < 1 || o.max_degree < o.min_degree ||
       o.max_restarts < 0 || k > 63 || (o.precision == FV_FP32 && !(o.low_tol > 0.0)) || !(o.euler_dt >= 0.0) ||
-      (o.euler_dt > 0.0 && (o.inner_m < 1 || o.inner_m > 500 || o.inner_max < 2 || !(o.inner_tol >= 0.0))))
+      (o.euler_dt > 0.0 && (o.inner_m < 1 || o.inner_m > 500 || o.inner_max < 2 || !(o.inner_tol >= 0.0))) ||
+      o.vecs_fp64 < 0 || o.vecs_fp64 > 1)
     return invalid("bad Arnoldi options (need 1 <= k <= 63, k + guard + 2 <= m <= 200)");
   if (o.precision != FV_FP64 && o.precision != FV_FP32) return invalid("precision must be FV_FP64 or FV_FP32");
   fv_arnoldi_report rep;

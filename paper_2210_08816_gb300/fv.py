@@ -47,7 +47,7 @@ class fv_arnoldi_opts(C.Structure):
                 ("max_degree", C.c_int), ("min_degree", C.c_int), ("guard", C.c_int),
                 ("seed", C.c_ulonglong), ("sigma", C.c_double), ("low_tol", C.c_double),
                 ("low_max_restarts", C.c_int), ("euler_dt", C.c_double), ("inner_m", C.c_int),
-                ("inner_max", C.c_int), ("inner_tol", C.c_double)]
+                ("inner_max", C.c_int), ("inner_tol", C.c_double), ("vecs_fp64", C.c_int)]
 
 
 class fv_arnoldi_report(C.Structure):
@@ -456,7 +456,7 @@ def arnoldi_leading(g: Grid, k, Gr, q, opts: fv_arnoldi_opts | None = None, vecs
     rep = fv_arnoldi_report()
     vp = None
     if vecs is not None:
-        vp = _ptr(vecs, g.dtype(o.precision), (k + 1) * g.n, "vecs")
+        vp = _ptr(vecs, g.dtype(FV_FP64 if o.vecs_fp64 else o.precision), (k + 1) * g.n, "vecs")
     st = lib().arnoldi_leading(g.h, int(k), float(Gr), _ptr(q, torch.float64, g.n, "q"), C.byref(o), re, im, vp,
                                C.byref(rep))
     _check(st, "arnoldi_leading", ok=(FV_OK, FV_ENOCONV))

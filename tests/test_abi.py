@@ -54,8 +54,8 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(fv.fv_grid_desc) == 3 * 4 + 4 + 3 * 8 + 2 * 8
     # precond, forcing, then the pseudo-time step (double)
     assert ctypes.sizeof(fv.fv_newton_opts) == 4 + 4 + 2 * 8 + 3 * 4 + 4 + 2 * 8 + 4 + 4 + 8
-    # ..., euler_dt, inner_m, inner_max, inner_tol
-    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4 + 8
+    # ..., euler_dt, inner_m, inner_max, inner_tol, vecs_fp64 (+4 padding)
+    assert ctypes.sizeof(fv.fv_arnoldi_opts) == 4 + 4 + 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4
     # ..., seconds, restarts_low (+4 padding), matvecs_low, matvecs_fp64, solves, solves_short, solve_worst
     assert ctypes.sizeof(fv.fv_arnoldi_report) == (4 + 4 + 4 + 4 + 8 + 3 * 64 * 8 + 256 * 4 + 8 + 4 + 4 + 8 + 8
                                                    + 4 + 4 + 8)
