@@ -169,6 +169,8 @@ def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30, atol=0.
         lam = 1.0
         for _ in range(7):
             qt = [q[c] + lam * dq[c] for c in range(4)]
+            if symmetric:  # near a symmetry-breaking crossing dq carries a large antisymmetric part
+                qt = symmetrise(qt)
             with np.errstate(all="ignore"):
                 Ft = D.pack(D.residual_full(grid, Gr, qt))
             if np.all(np.isfinite(Ft)):
@@ -176,7 +178,7 @@ def newton_direct(grid: D.Grid, Gr: float, q0, tol=1e-11, max_newton=30, atol=0.
                 if rt < rn:
                     break
             lam *= 0.5
-        q = symmetrise(qt) if symmetric else qt
+        q = qt
     return q, {"status": "max_newton", "residual": hist, "steps": max_newton}
 
 

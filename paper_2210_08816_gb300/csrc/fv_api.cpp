@@ -542,7 +542,8 @@ static int bicgstab2(Operator<R>& A, const R* b, R* x, double tol, int max_mv, R
 
 // Restarted GMRES(m) from the initial guess in x, classical Gram-Schmidt applied twice.
 template <typename R>
-static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv, R* basis, R* w, SolveInfo& info) {
+static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv, R* basis, R* w, SolveInfo& info,
+                 bool stop_on_stall = false) {
   Vec<R> V{A.g, 4 * A.g->N};
   const size_t n = V.n;
   fv_grid_s* g = A.g;
@@ -572,9 +573,9 @@ static int gmres(Operator<R>& A, const R* b, R* x, double tol, int m, int max_mv
       return FV_OK;
     }
     if (info.matvecs >= max_mv) return FV_OK;
-    // a restart cycle that left the true residual nearly where it was: the solve sits at its round-off
-    // floor (FP32 data) or stagnates; stop rather than spend the product budget
-    if (info.rel > 0.9 * rel_cycle) {
+    // (stop_on_stall) a restart cycle that left the true residual nearly where it was: the solve sits at
+    // its round-off floor (FP32 data) or stagnates; stop rather than spend the product budget
+    if (stop_on_stall && info.rel > 0.9 * rel_cycle) {
       info.stalled = true;
       return FV_OK;
     }
@@ -1567,7 +1568,7 @@ struct EulerRefine {
       FV_TRY(launch_convert(g, n, t64, b32));
       FV_TRY(V32.zero(x32));
       SolveInfo info;
-      FV_TRY(gmres<float>(A32, b32, x32, tol32, inner_m, inner_max, basis32, w32, info));
+      FV_TRY(gmres<float>(A32, b32, x32, tol32, inner_m, inner_max, basis32, w32, info, true));
       FV_TRY(apply_precond<float>(g, x32, pre32, s));
       FV_TRY(launch_convert(g, n, pre32, t64));
       FV_TRY(project_inplace<double>(g, t64, 1, 0.0, nullptr, nullptr));
@@ -1673,7 +1674,7 @@ static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const f
     }
     FV_TRY(V.zero(out));
     SolveInfo info;
-    FV_TRY(gmres<R>(Ae, in, out, etol, o.inner_m, o.inner_max, gbasis.p, gw.p, info));
+    FV_TRY(gmres<R>(Ae, in, out, etol, o.inner_m, o.inner_max, gbasis.p, gw.p, info, true));
     sstats.note(info.status == FV_OK, info.rel);
     FV_TRY(apply_precond<R>(g, out, epre.p, s));
     return V.copy(out, epre.p);

