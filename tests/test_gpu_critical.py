@@ -1,0 +1,82 @@
+"""Critical-Gr tracking (Section 4.1, Table 1) through the C-ABI against the oracle.
+
+On a 12^3 tanh-stretched grid at Pr = 0.015 a steady (real) mode and an oscillatory (complex) mode cross
+between Gr = 3.9e5 and 4.4e5.  The oracle located both crossings by bisection with its own steady states
+(sparse-LU Newton) and eigenvalues (ARPACK shift-invert), tests/golden/make_critical_gr.py.  fv_critical_gr
+(GPU Newton, implicit-Euler Arnoldi, secant / Illinois) must land on the same critical values: Gr_cr to
+1e-6 relative (the eigenvalues are converged to 1e-9 of |lam| ~ 500, and dRe lam / dGr ~ 1e-3, so the
+crossing is located to ~1e-9; the bound leaves room for the stopping rule), and the critical angular
+frequency of the oscillatory mode to 1e-6.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.discretisation as D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_08816_gb300 import build
+    build.build()
+    from paper_2210_08816_gb300 import fv as _fv
+    _fv.lib()
+    return _fv
+
+
+def _golden():
+    rows = {}
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "critical_gr_12_pr0.015.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            mode, gcr, lr, li = ln.split()
+            rows[mode] = (float(gcr), float(lr), float(li))
+    return rows
+
+
+@pytest.fixture(scope="module")
+def start(fv):
+    og = D.Grid(12, 12, 12, stretch=1.5, Pr=0.015)
+    g = fv.Grid(12, 12, 12, stretch=1.5, Pr=0.015)
+    q = torch.tensor(np.stack(D.to_api(og, D.conduction_state(og))), dtype=torch.float64,
+                     device="cuda").contiguous().view(-1)
+    o = fv.fv_newton_default_opts()
+    o.tol = 1e-12
+    o.max_newton = 40
+    o.gr_start, o.gr_ratio = 1.25e4, 2.0
+    st, rep = fv.newton_steady(g, 3.9e5, q, o)
+    assert st == fv.FV_OK, list(rep.history[:rep.newton_steps + 1])
+    return g, q
+
+
+@pytest.mark.parametrize("mode", ["real", "oscillatory"])
+def test_critical_gr_matches_oracle(fv, start, mode):
+    g, q0 = start
+    ref_gr, _, ref_im = _golden()[mode]
+    c = fv.fv_critical_default_opts()
+    c.gr_a, c.gr_b = 3.9e5, 4.4e5
+    c.tol = 1e-9
+    c.mode = fv.FV_MODE_REAL if mode == "real" else fv.FV_MODE_OSCILLATORY
+    a = fv.fv_arnoldi_default_opts()
+    a.euler_dt = 1e-4
+    a.m = 30
+    a.tol = 1e-10
+    a.max_restarts = 20
+    n = fv.fv_newton_default_opts()
+    n.tol = 1e-12
+    q = q0.clone()
+    st, rep = fv.fv_critical_gr(g, 6, q, c, nopts=n, aopts=a)
+    hist = [(rep.gr[i], rep.re[i], rep.im[i]) for i in range(rep.evaluations)]
+    assert st == fv.FV_OK, hist
+    assert rep.gr_cr == pytest.approx(ref_gr, rel=1e-6), hist
+    assert abs(rep.lam_re) <= 1e-4 * abs(complex(rep.lam_re, rep.lam_im)) + 1e-6
+    if mode == "oscillatory":
+        assert rep.lam_im == pytest.approx(ref_im, rel=1e-6)
+        assert rep.omega_scaled == pytest.approx(rep.lam_im / np.sqrt(rep.gr_cr), rel=1e-14)
+    else:
+        assert rep.lam_im == 0.0
