@@ -1709,7 +1709,7 @@ static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const f
   }
   FV_TRY(project_inplace<R>(g, x, 1, 0.0, nullptr, nullptr));
   const double etol_floor = o.inner_tol > 0.0 ? o.inner_tol : (mixed ? 1e-3 : std::max(1e-12, 0.01 * o.tol));
-  double worst_prev = 1.0, best = 1e300;
+  double best = 1e300;
   int best_at = 0, p = 0, status = FV_ENOCONV, nret = 0;
   std::vector<double> Gm, Hg, Qg, hre, him, sh;
   for (int restart = 0; restart <= o.max_restarts; ++restart) {
@@ -1908,7 +1908,6 @@ static int arnoldi_si(fv_grid_s* g, int k, double Gr, const double* q64, const f
       best_at = restart;
     }
     const bool stalled = stall > 0 && restart - best_at >= stall;
-    worst_prev = worst;
     if (all || mm < m || restart == o.max_restarts || stalled) {
       status = all ? FV_OK : FV_ENOCONV;
       // order by real part (then |Im|), +Im first; unit-norm vectors in that order into vecs_out
