@@ -845,8 +845,8 @@ static int jvp_project_block(fv_grid_s* g, double Gr, double sigma, const R* q, 
   if constexpr (sizeof(R) == 4) {
     if (pair) FV_TRY(launch_stencil_pair(g, Gr, sigma, q, V, Y, nvec));
   }
-  if (!pair)
-    for (int i = 0; i < nvec; ++i) FV_TRY(launch_jvp<R>(g, Gr, sigma, q, V + i * n4, Y + i * n4));
+  (void)n4;
+  if (!pair) FV_TRY(launch_jvp_block<R>(g, Gr, sigma, q, V, Y, nvec));
   FV_TRY(launch_divergence<R>(g, Y, phi, nvec));
   FV_TRY(launch_poisson_block<R>(g, phi, phi, tmp, nvec));
   FV_TRY(launch_correct_block<R>(g, Y, phi, sigma != 0.0 ? V : nullptr, sigma, W, nvec));

@@ -165,6 +165,9 @@ template <typename R>
 int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F);
 template <typename R>
 int launch_jvp(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);
+// The one-cell J.v stencil over nvec states stored one after another in v and out (4N each), one launch.
+template <typename R>
+int launch_jvp_block(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out, int nvec);
 // nvec > 1: vel holds nvec states (4N each) and rhs nvec fields (N each), one after another.
 template <typename R>
 int launch_divergence(const fv_grid_s* g, const R* vel, R* rhs, int nvec = 1);

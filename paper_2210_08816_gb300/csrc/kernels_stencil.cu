@@ -391,7 +391,7 @@ template <typename R, int MODE>
 __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
     k_stencil_z(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmv, int use_tma,
                 int* err, long long spins, Geo<R> g, int N, R Gr, R invPr, R sigma, const R* __restrict__ q, const R* __restrict__ v,
-                R* __restrict__ out) {
+                R* __restrict__ out, int nch) {
   constexpr int NA = (MODE == 0) ? 4 : 8;
   constexpr int AB = (MODE == 0) ? 0 : 4;
   constexpr int NWARP = kTX * kTY / 32;
@@ -402,7 +402,12 @@ __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
   const int tid = threadIdx.x;
   const int tx = tid % kTX, ty = tid / kTX;
   const int warp = tid / 32, lane = tid % 32;
-  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kZChunk;
+  // blockIdx.z = z-chunk + nch * vector: vector `vec` of a block of states stored one after another in v and
+  // out (4N elements each); its fields are fields 4 vec .. 4 vec + 3 of the tensor map tmv
+  const int vec = (int)blockIdx.z / nch;
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = ((int)blockIdx.z - vec * nch) * kZChunk;
+  v += (size_t)vec * 4 * N;
+  out += (size_t)vec * 4 * N;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int kend = min(k0 + kZChunk, nz);
   if (use_tma && tid == 0) {
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(kTX * kTY, sizeof(R) == 4 ? 3 : 2)
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
                 "%4, %5, %6}], [%2];" ::"r"(smem_addr(slot + 4 * kPL)),
-                "l"(reinterpret_cast<uint64_t>(&tmv)), "r"(b), "r"(i0 - kX0), "r"(j0 - 1), "r"(kk), "r"(0)
+                "l"(reinterpret_cast<uint64_t>(&tmv)), "r"(b), "r"(i0 - kX0), "r"(j0 - 1), "r"(kk), "r"(4 * vec)
                 : "memory");
         }
       } else {  // a plane outside the domain: zeros, and a plain arrival completes the barrier phase
@@ -824,9 +829,9 @@ inline void cell_grid(const fv_grid_s* g, dim3& grid, dim3& block) {
 
 // 4D tensor map of one state (x, y, z, field) with boxes of kPW x kHY x 1 x 4 elements
 template <typename R>
-int state_map(const fv_grid_s* g, const R* ptr, CUtensorMap* m) {
+int state_map(const fv_grid_s* g, const R* ptr, CUtensorMap* m, int nvec = 1) {
   const size_t sz = sizeof(R);
-  const uint64_t dims[4] = {(uint64_t)g->nx, (uint64_t)g->ny, (uint64_t)g->nz, 4};
+  const uint64_t dims[4] = {(uint64_t)g->nx, (uint64_t)g->ny, (uint64_t)g->nz, 4 * (uint64_t)nvec};
   const uint64_t strides[3] = {g->nx * sz, (uint64_t)g->nx * g->ny * sz, g->N * sz};
   const uint32_t box[4] = {(uint32_t)kPW, (uint32_t)kHY, 1, 4};
   return encode_tensor_map(m, sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
@@ -834,7 +839,7 @@ int state_map(const fv_grid_s* g, const R* ptr, CUtensorMap* m) {
 }
 
 template <typename R, int MODE>
-int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out) {
+int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out, int nvec = 1) {
   constexpr int NA = (MODE == 0) ? 4 : 8;
   const size_t smem = (size_t)NA * kRing * kPL * sizeof(R);
   static bool attr_set = false;
@@ -848,11 +853,16 @@ int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, co
   std::memset(&tv, 0, sizeof(tv));
   int use_tma = ((g->nx * sizeof(R)) % 16 == 0 && g->nx >= 64 && g->ny >= 16 && ((uintptr_t)q % 16) == 0 &&
                  ((uintptr_t)v % 16) == 0) ? 1 : 0;
-  if (use_tma && (state_map<R>(g, q, &tq) != FV_OK || state_map<R>(g, v, &tv) != FV_OK)) use_tma = 0;
-  dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTY - 1) / kTY, (g->nz + kZChunk - 1) / kZChunk);
+  if (use_tma && (state_map<R>(g, q, &tq) != FV_OK || state_map<R>(g, v, &tv, nvec) != FV_OK)) use_tma = 0;
+  const int nch = (g->nz + kZChunk - 1) / kZChunk;
+  if (nvec < 1 || (long long)nch * nvec > 65535) {
+    set_error("launch_stencil_z: too many vectors in one block");
+    return FV_EINVAL;
+  }
+  dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTY - 1) / kTY, nch * nvec);
   ProfScope ps(g, PROF_STENCIL);
   k_stencil_z<R, MODE><<<grid, kTX * kTY, smem, g->stream>>>(tq, tv, use_tma, g->ws.err, wait_spins(g), geo_of<R>(g), (int)g->N,
-                                                             (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out);
+                                                             (R)Gr, (R)(1.0 / g->Pr), (R)sigma, q, v, out, nch);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -860,6 +870,11 @@ int launch_stencil_z(const fv_grid_s* g, double Gr, double sigma, const R* q, co
 template <typename R>
 int launch_residual(const fv_grid_s* g, double Gr, const R* q, R* F) {
   return launch_stencil_z<R, 0>(g, Gr, 0.0, q, q, F);
+}
+
+template <typename R>
+int launch_jvp_block(const fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out, int nvec) {
+  return launch_stencil_z<R, 1>(g, Gr, sigma, q, v, out, nvec);
 }
 
 template <typename R>
@@ -955,6 +970,8 @@ int launch_correct(const fv_grid_s* g, const R* Y, const R* phi, double alpha, c
 template int launch_residual<double>(const fv_grid_s*, double, const double*, double*);
 template int launch_jvp<double>(const fv_grid_s*, double, double, const double*, const double*, double*);
 template int launch_jvp<float>(const fv_grid_s*, double, double, const float*, const float*, float*);
+template int launch_jvp_block<double>(const fv_grid_s*, double, double, const double*, const double*, double*, int);
+template int launch_jvp_block<float>(const fv_grid_s*, double, double, const float*, const float*, float*, int);
 template int launch_divergence<double>(const fv_grid_s*, const double*, double*, int);
 template int launch_divergence<float>(const fv_grid_s*, const float*, float*, int);
 template int launch_correct_block<double>(const fv_grid_s*, const double*, const double*, const double*, double,
