@@ -350,7 +350,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // shared-memory ring's phases run on across tiles (global stage counter), and two TMEM accumulators
 // (columns 0 and 256) let a separate epilogue warpgroup drain tile t while the MMAs of tile t + 1 run.
 // Warps: 0 TMA producer, 1 MMA issuer, 2-5 converters (row t of the A tiles), 6-9 epilogue.
+// Barriers per step gi: full (TMA landed) -> conv (hi in place, lo in slot gi % 2) -> MMAs, whose commits
+// free the TMA stage (empty) and the remainder slot (lofree) for step gi + 4 and gi + 2.
 constexpr int kTcpThreads = 320;
+// Ring depths of the persistent pass: the TMA ring (A slabs and B slabs, written by TMA) runs four stages
+// deep; the converters' TF32 remainders of A live in a separate two-slot ring, so the bytes in flight from
+// DRAM per SM grow by a third within the same shared memory.
+constexpr int kTcpStages = 4;
+constexpr int kTcpLoSlots = 2;
 constexpr bool kTcPersistent = true;  // the one-tile-per-CTA kernel above stays as the reference form
 
 template <bool SCALE, bool BWD>
@@ -361,25 +368,27 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                     const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
                     int* err, long long spins) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_conv[kTcStages], bar_empty[kTcStages];
-  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_drain;
+  __shared__ __align__(8) uint64_t bar_full[kTcpStages], bar_conv[kTcpStages], bar_empty[kTcpStages];
+  __shared__ __align__(8) uint64_t bar_lofree[kTcpLoSlots], bar_accf[2], bar_acce[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ float lz_s[256];
   const int h = n / 2;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t b_bytes = (uint32_t)h * kTcRowBytes;
-  const uint32_t stage_bytes = 4u * kTcABytes + 4u * b_bytes;
+  const uint32_t stage_bytes = 2u * kTcABytes + 4u * b_bytes;  // [A1 | A2 | B1hi | B1lo | B2hi | B2lo]
+  const uint32_t lo_base = base + kTcpStages * stage_bytes;  // slot s: [L1 | L2] at lo_base + s * 2 A slabs
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nst = n / (2 * kTcBK);
   const int ntiles = (Ptot + kTcBM - 1) / kTcBM;
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < kTcpStages; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_conv[s]), 128);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
+    for (int s = 0; s < kTcpLoSlots; ++s) mbar_init(smem_u32(&bar_lofree[s]), 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_accf[b]), 1);
       mbar_init(smem_u32(&bar_acce[b]), 4);  // one arrival per epilogue warp
@@ -406,8 +415,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       for (int ti = 0; ti < my_tiles && ok; ++ti) {
         const int p0 = ((int)blockIdx.x + ti * (int)gridDim.x) * kTcBM;
         for (int j = 0; j < nst; ++j) {
-          const int gi = ti * nst + j, st = gi % kTcStages;
-          if (gi >= kTcStages && !mbar_wait(smem_u32(&bar_empty[st]), ((gi / kTcStages) - 1) & 1, err, 11, spins)) {
+          const int gi = ti * nst + j, st = gi % kTcpStages;
+          if (gi >= kTcpStages && !mbar_wait(smem_u32(&bar_empty[st]), ((gi / kTcpStages) - 1) & 1, err, 11, spins)) {
             ok = false;
             break;
           }
@@ -418,16 +427,16 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
           mbar_expect_tx(fb, 2u * kTcABytes + 4u * b_bytes);
           tma_load_2d(sb, &tmA, fb, k1, p0);
           tma_load_2d(sb + kTcABytes, &tmA, fb, k2, p0);
-          tma_load_2d(sb + 4u * kTcABytes, &tmB1hi, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 4u * kTcABytes + b_bytes, &tmB1lo, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 4u * kTcABytes + 2u * b_bytes, &tmB2hi, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 4u * kTcABytes + 3u * b_bytes, &tmB2lo, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 2u * kTcABytes, &tmB1hi, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 2u * kTcABytes + b_bytes, &tmB1lo, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 2u * kTcABytes + 2u * b_bytes, &tmB2hi, fb, j * kTcBK, 0);
+          tma_load_2d(sb + 2u * kTcABytes + 3u * b_bytes, &tmB2lo, fb, j * kTcBK, 0);
           ++issued;
         }
       }
       // drain: every issued copy has landed before the block may exit
-      for (int gi = (issued > kTcStages ? issued - kTcStages : 0); gi < issued; ++gi)
-        mbar_wait(smem_u32(&bar_full[gi % kTcStages]), (gi / kTcStages) & 1, err, 12, kWaitLimit);
+      for (int gi = (issued > kTcpStages ? issued - kTcpStages : 0); gi < issued; ++gi)
+        mbar_wait(smem_u32(&bar_full[gi % kTcpStages]), (gi / kTcpStages) & 1, err, 12, kWaitLimit);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -444,17 +453,18 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dacc = tmem + (uint32_t)(b * 256);
         for (int j = 0; j < nst; ++j) {
-          const int gi = ti * nst + j, st = gi % kTcStages;
-          if (!mbar_wait(smem_u32(&bar_conv[st]), (gi / kTcStages) & 1, err, 14, spins)) {
+          const int gi = ti * nst + j, st = gi % kTcpStages;
+          if (!mbar_wait(smem_u32(&bar_conv[st]), (gi / kTcpStages) & 1, err, 14, spins)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sb = base + st * stage_bytes;
+          const uint32_t lb = lo_base + (uint32_t)(gi % kTcpLoSlots) * (2u * kTcABytes);
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
-            const uint32_t a_hi = sb + half * kTcABytes, a_lo = sb + (2 + half) * kTcABytes;
-            const uint32_t b_hi = sb + 4u * kTcABytes + (2 * half) * b_bytes, b_lo = b_hi + b_bytes;
+            const uint32_t a_hi = sb + half * kTcABytes, a_lo = lb + half * kTcABytes;
+            const uint32_t b_hi = sb + 2u * kTcABytes + (2 * half) * b_bytes, b_lo = b_hi + b_bytes;
             const uint32_t d = dacc + (uint32_t)(half * h);
 #pragma unroll
             for (int kk = 0; kk < kTcBK / 8; ++kk) {
@@ -466,6 +476,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             }
           }
           mma_commit(smem_u32(&bar_empty[st]));
+          mma_commit(smem_u32(&bar_lofree[gi % kTcpLoSlots]));  // the remainder slot is free again
         }
         mma_commit(smem_u32(&bar_accf[b]));  // arrives once every MMA issued so far has completed
         last = ti;
@@ -479,22 +490,30 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
       }
     }
   } else if (warp < 6) {
-    // converters: thread t owns row t of every stage's A tiles
+    // converters: thread t owns row t of every stage's A tiles and of every remainder slot
     const int t = threadIdx.x - 64;
     const int x = (t >> 1) & 3;  // swizzle pattern of this row
     bool ok = true;
     for (int ti = 0; ti < my_tiles && ok; ++ti) {
       for (int j = 0; j < nst; ++j) {
-        const int gi = ti * nst + j, st = gi % kTcStages;
-        if (!mbar_wait(smem_u32(&bar_full[st]), (gi / kTcStages) & 1, err, 17, spins)) {
+        const int gi = ti * nst + j, st = gi % kTcpStages, ls = gi % kTcpLoSlots;
+        if (!mbar_wait(smem_u32(&bar_full[st]), (gi / kTcpStages) & 1, err, 17, spins)) {
+          ok = false;
+          break;
+        }
+        // the remainder slot was last read by the MMAs of step gi - kTcpLoSlots
+        if (gi >= kTcpLoSlots &&
+            !mbar_wait(smem_u32(&bar_lofree[ls]), ((gi / kTcpLoSlots) - 1) & 1, err, 19, spins)) {
           ok = false;
           break;
         }
         unsigned char* sp = smem_raw + ((base + st * stage_bytes) - smem_u32(smem_raw)) + t * kTcRowBytes;
+        unsigned char* lp =
+            smem_raw + ((lo_base + ls * 2u * kTcABytes) - smem_u32(smem_raw)) + t * kTcRowBytes;
         float4* a1 = reinterpret_cast<float4*>(sp);
         float4* a2 = reinterpret_cast<float4*>(sp + kTcABytes);
-        float4* l1 = reinterpret_cast<float4*>(sp + 2 * kTcABytes);
-        float4* l2 = reinterpret_cast<float4*>(sp + 3 * kTcABytes);
+        float4* l1 = reinterpret_cast<float4*>(lp);
+        float4* l2 = reinterpret_cast<float4*>(lp + kTcABytes);
         if (BWD) {  // chunks in the swizzled order: no bank conflicts
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -647,6 +666,10 @@ int encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, cons
 namespace {
 
 size_t tc_smem_bytes(int n) { return (size_t)kTcStages * (4 * kTcABytes + 4 * (size_t)(n / 2) * kTcRowBytes) + 1024; }
+size_t tcp_smem_bytes(int n) {
+  return (size_t)kTcpStages * (2 * kTcABytes + 4 * (size_t)(n / 2) * kTcRowBytes) +
+         (size_t)kTcpLoSlots * 2 * kTcABytes + 1024;
+}
 
 }  // namespace
 
@@ -764,9 +787,10 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<dou
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  const int smemp_max = (int)tcp_smem_bytes(256);
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemp_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemp_max));
+  FV_CUDA(cudaFuncSetAttribute(k_transform_tcp<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemp_max));
   {
     int dev = 0, sms = 0;
     FV_CUDA(cudaGetDevice(&dev));
@@ -798,16 +822,17 @@ int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float*
   const CUtensorMap* B = g->tc.B[axis] + (bwd ? 4 : 0);
   ProfScope ps(g, PROF_TRANSFORM_TC);
   if (kTcPersistent && g->tc.sms > 0) {
+    const size_t smemp = tcp_smem_bytes(n);
     const dim3 pgrid((unsigned)std::min<long long>(ntiles, g->tc.sms));
     if (bwd)
-      k_transform_tcp<false, true><<<pgrid, kTcpThreads, smem, g->stream>>>(
+      k_transform_tcp<false, true><<<pgrid, kTcpThreads, smemp, g->stream>>>(
           tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     else if (scale)
-      k_transform_tcp<true, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
+      k_transform_tcp<true, false><<<pgrid, kTcpThreads, smemp, g->stream>>>(
           tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb,
           g->ws.err, wait_spins(g));
     else
-      k_transform_tcp<false, false><<<pgrid, kTcpThreads, smem, g->stream>>>(
+      k_transform_tcp<false, false><<<pgrid, kTcpThreads, smemp, g->stream>>>(
           tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     FV_CUDA(cudaGetLastError());
     return FV_OK;
