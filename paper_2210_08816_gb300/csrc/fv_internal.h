@@ -80,6 +80,9 @@ struct TcState {
   // per axis: [fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi, bwd_s_lo, bwd_a_hi, bwd_a_lo]
   CUtensorMap B[3][8];
   const float* lam[3] = {nullptr, nullptr, nullptr};  // eigenvalues in the tensor-core mode order
+  // per axis and direction (0 forward, 1 backward): the four B matrices of every K step laid out as the
+  // shared-memory stage holds them (64-byte swizzled rows), one contiguous block per step
+  const unsigned char* Bsw[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   int sms = 0;  // multiprocessors of the device (grid of the persistent passes)
 };
 }  // namespace fv

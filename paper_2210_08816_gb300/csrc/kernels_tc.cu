@@ -92,6 +92,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Plain bulk copy global -> shared (contiguous bytes, 16-byte aligned ends), completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
@@ -362,11 +369,9 @@ constexpr bool kTcPersistent = true;  // the one-tile-per-CTA kernel above stays
 
 template <bool SCALE, bool BWD>
 __global__ void __launch_bounds__(kTcpThreads, 1)
-    k_transform_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB1hi,
-                    const __grid_constant__ CUtensorMap tmB1lo, const __grid_constant__ CUtensorMap tmB2hi,
-                    const __grid_constant__ CUtensorMap tmB2lo, float* __restrict__ out, int P, int Ptot, int n,
-                    const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz, int nb,
-                    int* err, long long spins) {
+    k_transform_tcp(const __grid_constant__ CUtensorMap tmA, const unsigned char* __restrict__ bsw,
+                    float* __restrict__ out, int P, int Ptot, int n, const float* __restrict__ lx,
+                    const float* __restrict__ ly, const float* __restrict__ lz, int nb, int* err, long long spins) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kTcpStages], bar_conv[kTcpStages], bar_empty[kTcpStages];
   __shared__ __align__(8) uint64_t bar_lofree[kTcpLoSlots], bar_accf[2], bar_acce[2], bar_drain;
@@ -427,10 +432,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
           mbar_expect_tx(fb, 2u * kTcABytes + 4u * b_bytes);
           tma_load_2d(sb, &tmA, fb, k1, p0);
           tma_load_2d(sb + kTcABytes, &tmA, fb, k2, p0);
-          tma_load_2d(sb + 2u * kTcABytes, &tmB1hi, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 2u * kTcABytes + b_bytes, &tmB1lo, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 2u * kTcABytes + 2u * b_bytes, &tmB2hi, fb, j * kTcBK, 0);
-          tma_load_2d(sb + 2u * kTcABytes + 3u * b_bytes, &tmB2lo, fb, j * kTcBK, 0);
+          // the four B slabs of step j, already in the stage's swizzled layout: one contiguous copy
+          bulk_load(sb + 2u * kTcABytes, bsw + (size_t)j * 4u * b_bytes, 4u * b_bytes, fb);
           ++issued;
         }
       }
@@ -691,12 +694,15 @@ bool tc_eligible(const fv_grid_s* g) {
 //   forward  F_s[s][k] = sqrt(w_k / 2) y_s[k],   F_a[a][k] = sqrt(w_k / 2) y_a[k]     (k < h)
 //   backward E_s[i][s] = y_s[i] / sqrt(2 w_i),   E_a[i][a] = y_a[i] / sqrt(2 w_i)     (i < h)
 // plus the eigenvalues in that order.  Buffer: [axis][fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi,
-// bwd_s_lo, bwd_a_hi, bwd_a_lo][h x h], then [axis][lambda (n)].
+// bwd_s_lo, bwd_a_hi, bwd_a_lo][h x h], then [axis][lambda (n)], then the swizzled step blocks below.
 int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<double>* idc) {
   const int ns[3] = {g->nx, g->ny, g->nz};
   size_t total = 0;
   for (int d = 0; d < 3; ++d) total += 8 * (size_t)(ns[d] / 2) * (ns[d] / 2) + ns[d];
-  std::vector<float> hbuf(total);
+  const size_t sw_start = (total + 63) & ~(size_t)63;  // swizzled step blocks: 256-byte aligned
+  total = sw_start;
+  for (int d = 0; d < 3; ++d) total += 8 * (size_t)(ns[d] / 2) * (ns[d] / 2);
+  std::vector<float> hbuf(total, 0.0f);
   size_t o = 0;
   size_t moff[3][8], loff[3];
   auto put_split = [&](const std::vector<double>& M, size_t& ohi, size_t& olo, size_t cnt) {
@@ -770,6 +776,34 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<dou
     loff[d] = o;
     for (int m = 0; m < ns[d]; ++m) hbuf[o++] = (float)lam_tc[d][m];
   }
+  // The persistent pass's B operands, per axis and direction: for every K step j the four slabs
+  // [s_hi | s_lo | a_hi | a_lo] of rows 0..h-1 and columns 16 j .. 16 j + 15, each row's four 16-byte
+  // chunks in the 64-byte swizzled order that a tensor-map copy into a 1024-byte aligned stage produces
+  // (chunk c of row r at position c ^ ((r >> 1) & 3)), so that one contiguous bulk copy fills a stage.
+  o = sw_start;
+  size_t soff[3][2];
+  for (int d = 0; d < 3; ++d) {
+    const int h = ns[d] / 2, nstp = h / kTcBK;
+    for (int dir = 0; dir < 2; ++dir) {
+      soff[d][dir] = o;
+      for (int j = 0; j < nstp; ++j)
+        for (int m = 0; m < 4; ++m) {
+          const size_t src = moff[d][4 * dir + m];
+          const size_t dst = o + (size_t)(j * 4 + m) * h * kTcBK;
+          for (int r = 0; r < h; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const int pc = c ^ ((r >> 1) & 3);
+              for (int e = 0; e < 4; ++e)
+                hbuf[dst + (size_t)r * kTcBK + pc * 4 + e] = hbuf[src + (size_t)r * h + j * kTcBK + c * 4 + e];
+            }
+        }
+      o += (size_t)nstp * 4 * h * kTcBK;
+    }
+  }
+  if (o != total) {
+    set_error("tensor-core operand layout mismatch");
+    return FV_EINVAL;
+  }
   void* buf = nullptr;
   if (cudaMalloc(&buf, total * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
@@ -782,6 +816,7 @@ int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<dou
     const int h = ns[d] / 2;
     for (int j = 0; j < 8; ++j) FV_TRY(encode(&g->tc.B[d][j], (const float*)buf + moff[d][j], h, h, h));
     g->tc.lam[d] = (const float*)buf + loff[d];
+    for (int dir = 0; dir < 2; ++dir) g->tc.Bsw[d][dir] = (const unsigned char*)((const float*)buf + soff[d][dir]);
   }
   const int smem_max = (int)tc_smem_bytes(256);
   FV_CUDA(cudaFuncSetAttribute(k_transform_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
@@ -823,17 +858,18 @@ int tc_pass(const fv_grid_s* g, int axis, bool bwd, int na, int nb, const float*
   ProfScope ps(g, PROF_TRANSFORM_TC);
   if (kTcPersistent && g->tc.sms > 0) {
     const size_t smemp = tcp_smem_bytes(n);
+    const unsigned char* bsw = g->tc.Bsw[axis][bwd ? 1 : 0];
     const dim3 pgrid((unsigned)std::min<long long>(ntiles, g->tc.sms));
     if (bwd)
       k_transform_tcp<false, true><<<pgrid, kTcpThreads, smemp, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
+          tmA, bsw, out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     else if (scale)
       k_transform_tcp<true, false><<<pgrid, kTcpThreads, smemp, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb,
-          g->ws.err, wait_spins(g));
+          tmA, bsw, out, (int)P, (int)Ptot, n, g->tc.lam[0], g->tc.lam[1], g->tc.lam[2], nb, g->ws.err,
+          wait_spins(g));
     else
       k_transform_tcp<false, false><<<pgrid, kTcpThreads, smemp, g->stream>>>(
-          tmA, B[0], B[1], B[2], B[3], out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
+          tmA, bsw, out, (int)P, (int)Ptot, n, nullptr, nullptr, nullptr, nb, g->ws.err, wait_spins(g));
     FV_CUDA(cudaGetLastError());
     return FV_OK;
   }
