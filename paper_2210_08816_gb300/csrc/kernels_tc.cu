@@ -360,8 +360,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Barriers per step gi: full (TMA landed) -> conv (hi in place, lo in slot gi % 2) -> MMAs, whose commits
 // free the TMA stage (empty) and the remainder slot (lofree) for step gi + 4 and gi + 2.
 constexpr int kTcpThreads = 320;
-// Ring depths of the persistent pass: the TMA ring (A slabs and B slabs, written by TMA) runs four stages
-// deep; the converters' TF32 remainders of A live in a separate two-slot ring, so the bytes in flight from
+// Ring depths of the persistent pass: the TMA ring (A slabs by tensor copies, the step's B slabs by one
+// bulk copy of their pre-swizzled image) runs four stages deep; the converters' TF32 remainders of A live in a separate two-slot ring, so the bytes in flight from
 // DRAM per SM grow by a third within the same shared memory.
 constexpr int kTcpStages = 4;
 constexpr int kTcpLoSlots = 2;
