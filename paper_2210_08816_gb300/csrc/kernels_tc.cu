@@ -361,8 +361,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // free the TMA stage (empty) and the remainder slot (lofree) for step gi + 4 and gi + 2.
 constexpr int kTcpThreads = 320;
 // Ring depths of the persistent pass: the TMA ring (A slabs by tensor copies, the step's B slabs by one
-// bulk copy of their pre-swizzled image) runs four stages deep; the converters' TF32 remainders of A live in a separate two-slot ring, so the bytes in flight from
-// DRAM per SM grow by a third within the same shared memory.
+// bulk copy of their pre-swizzled image) runs four stages deep; the converters' TF32 remainders of A live
+// in a separate two-slot ring, so the bytes in flight from DRAM per SM grow by a third within the same
+// shared memory.
 constexpr int kTcpStages = 4;
 constexpr int kTcpLoSlots = 2;
 constexpr bool kTcPersistent = true;  // the one-tile-per-CTA kernel above stays as the reference form
