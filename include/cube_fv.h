@@ -258,14 +258,15 @@ typedef struct {
                              J.v+projection in FP32; residual, updates and inner
                              products FP64 (the outer loop refines to FP64); inner
                              tolerances are kept >= 1e-3 (preconditioned) or 1e-5 */
-    double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) */
-    double krylov_tol;    /* relative residual of each inner solve (forcing = 0), or its floor */
-    int max_newton;       /* Newton steps */
+    double tol;           /* stop when ||P F||_inf <= tol * max(1, ||P F(q0)||_inf) (default 1e-10) */
+    double krylov_tol;    /* relative residual of each inner solve (forcing = 0), or its floor
+                             (default 1e-10) */
+    int max_newton;       /* Newton steps per Gr (default 20) */
     int max_matvec;       /* J.v+projections per inner solve (default 8000) */
     int gmres_m;          /* restart length of the GMRES fallback (default 100; 30 stalled at
                              64^3, Gr = 4e7) */
-    double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr */
-    double gr_ratio;      /* continuation factor per step (> 1) */
+    double gr_start;      /* > 0 and < Gr: continuation from gr_start up to Gr; 0 (default): none */
+    double gr_ratio;      /* continuation factor per step (> 1) (default 2) */
     int precond;          /* 1 (default): right preconditioner M^-1 = P L^-1, L the diffusion
                              operator of J inverted by fast diagonalisation (see
                              fv_diffusion_solve): inner iteration counts stay nearly flat as the
@@ -317,15 +318,16 @@ typedef struct {
                              FP64 cycles started from its Ritz vectors refine to tol (each FP64
                              cycle picks its polynomial degree by the same rule as the FP32
                              ones, clamped to [min_degree, max_degree]) */
-    int m;                /* Krylov subspace dimension per cycle */
+    int m;                /* Krylov subspace dimension per cycle (default 20) */
     double tol;           /* stop when every wanted Ritz pair has
-                             ||A x - lam x|| <= tol |lam| ||x|| (true residual, FP64 reductions) */
+                             ||A x - lam x|| <= tol |lam| ||x|| (true residual, FP64 reductions)
+                             (default 1e-9) */
     int max_restarts;     /* cycle cap (default 30) */
     int max_degree;       /* Chebyshev polynomial degree cap per cycle (default 200) */
     int min_degree;       /* (default 10) */
     int guard;            /* extra Ritz values kept outside the filter's ellipse (default 2) */
-    unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected */
-    double sigma;         /* shift of the gradient complement; 0 = automatic */
+    unsigned long long seed;   /* start vector: SplitMix64/Box-Muller N(0,1), projected (default 1) */
+    double sigma;         /* shift of the gradient complement; 0 (default): automatic */
     double low_tol;       /* FV_FP32: residual tolerance of the FP32 phase (default 1e-3); the phase
                              also ends once its largest residual has not halved in 3 cycles */
     int low_max_restarts; /* FV_FP32: cycle cap of the FP32 phase (default 20) */
