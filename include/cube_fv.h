@@ -428,6 +428,20 @@ void fv_critical_default_opts(fv_critical_opts* o);
 int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton_opts* nopts, const fv_arnoldi_opts* aopts,
                    const fv_critical_opts* copts, fv_critical_report* report);
 
+/* A tracked eigenvalue as a function of Gr, supplied by the caller: returns FV_OK and the value's real
+ * and imaginary parts at gr, or a nonzero status that ends the iteration. */
+typedef int (*fv_tracked_fn)(double gr, void* ctx, double* re, double* im);
+
+/* The root iteration of fv_critical_gr on a caller's function (Section 4.1), host only: evaluates f at
+ * gr_a and gr_b, then takes secant steps (each at most twice the last spacing) until two values of
+ * opposite sign bracket the crossing, then false-position steps with the Illinois halving of a retained
+ * end.  Stops with FV_OK once a step moves Gr by at most tol Gr (or hits an exact zero), FV_ENOCONV after
+ * max_iter steps or when two values coincide; a nonzero status of f ends it with that status.  `mode`
+ * is not used (f returns the tracked value itself).  report (host, may be NULL): every successful
+ * evaluation in order, gr_cr / lam_re / lam_im / omega_scaled at the last one.  Errors: FV_EINVAL (null
+ * f, gr_a or gr_b not > 0 or equal, tol not > 0, max_iter outside 0..38). */
+int fv_critical_root(const fv_critical_opts* copts, fv_tracked_fn f, void* ctx, fv_critical_report* report);
+
 /* Richardson extrapolation to zero grid size (Section 4.1: the critical values depend linearly on the
  * squared average grid size): the least-squares line value = limit + slope h2 through n >= 2 points
  * (h2[i], value[i]) (host arrays), e.g. h2 = (nx ny nz)^(-2/3).  limit, slope: host, either may be NULL.

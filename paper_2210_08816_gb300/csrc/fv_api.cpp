@@ -2493,12 +2493,108 @@ extern "C" void fv_critical_default_opts(fv_critical_opts* o) {
   o->mode = FV_MODE_LEADING;
 }
 
+namespace fv {
+
+// The root iteration on Re lam(Gr) (Section 4.1): secant steps, each limited to twice the last spacing,
+// until a sign change brackets the crossing, then false position with the Illinois halving of an end
+// that is retained twice in a row.  eval(gr, &re, &im) returns a status and the tracked eigenvalue; the
+// report keeps every successful evaluation and ends at the last one (gr_cr).  Returns the report's status.
+template <typename Eval>
+static int critical_root(const fv_critical_opts& c, Eval&& eval, fv_critical_report* rep) {
+  std::memset(rep, 0, sizeof(*rep));
+  rep->status = FV_ENOCONV;
+  double x = 0.0, fx = 0.0, ix = 0.0;  // the last successful evaluation
+  auto evaluate = [&](double gr, double* lr, double* li) -> int {
+    const int st = eval(gr, lr, li);
+    if (st != FV_OK) return st;
+    if (!std::isfinite(*lr) || !std::isfinite(*li)) {
+      set_error("critical Gr: non-finite tracked eigenvalue at Gr = " + std::to_string(gr));
+      return FV_ENAN;
+    }
+    if (rep->evaluations < 40) {
+      rep->gr[rep->evaluations] = gr;
+      rep->re[rep->evaluations] = *lr;
+      rep->im[rep->evaluations] = *li;
+    }
+    ++rep->evaluations;
+    x = gr;
+    fx = *lr;
+    ix = *li;
+    return FV_OK;
+  };
+  double fa = 0.0, ia = 0.0, fb = 0.0, ib = 0.0;
+  double a = c.gr_a, b = c.gr_b;
+  int st = evaluate(a, &fa, &ia);
+  if (st == FV_OK) st = evaluate(b, &fb, &ib);
+  int side = 0;  // Illinois: which end was kept last time (-1: a)
+  bool bracketed = st == FV_OK && fa * fb <= 0.0;
+  for (int it = 0; st == FV_OK && it < c.max_iter; ++it) {
+    if (fb == fa) break;
+    double xn = b - fb * (b - a) / (fb - fa);
+    if (!bracketed) {  // secant: keep the step within twice the current spacing
+      const double lim = 2.0 * std::fabs(b - a);
+      xn = std::min(std::max(xn, b - lim), b + lim);
+    }
+    if (!(xn > 0.0)) xn = 0.5 * std::min(a, b);
+    double fn, in;
+    st = evaluate(xn, &fn, &in);
+    if (st != FV_OK) break;
+    const bool done = std::fabs(xn - b) <= c.tol * std::fabs(b) || fn == 0.0;
+    // b is always the newest point; once a sign change is seen, a and b keep opposite signs
+    if (!bracketed && fn * fa < 0.0 && fn * fb > 0.0) {
+      bracketed = true;  // the crossing lies between a and xn: keep a
+      b = xn;
+      fb = fn;
+    } else if (!bracketed && fn * fb < 0.0) {
+      bracketed = true;  // between b and xn
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+      side = 0;
+    } else if (!bracketed) {  // secant step
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+    } else if (fn * fb < 0.0) {  // false position: the newest end changed sign, the old b becomes a
+      a = b;
+      fa = fb;
+      b = xn;
+      fb = fn;
+      side = 0;
+    } else {  // a is retained again: Illinois halves its value so that it is not retained forever
+      if (side == -1) fa *= 0.5;
+      side = -1;
+      b = xn;
+      fb = fn;
+    }
+    if (done) {
+      rep->status = FV_OK;
+      break;
+    }
+  }
+  if (rep->evaluations > 0) {
+    rep->gr_cr = x;
+    rep->lam_re = fx;
+    rep->lam_im = ix;
+    rep->omega_scaled = ix / std::sqrt(x);
+  }
+  if (st != FV_OK) rep->status = st;
+  return rep->status;
+}
+
+static bool critical_opts_ok(const fv_critical_opts& c) {
+  return c.gr_a > 0.0 && c.gr_b > 0.0 && c.gr_a != c.gr_b && c.tol > 0.0 && c.max_iter >= 0 && c.max_iter <= 38;
+}
+
+}  // namespace fv
+
 extern "C" int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton_opts* nopts,
                               const fv_arnoldi_opts* aopts, const fv_critical_opts* copts, fv_critical_report* report) {
   if (!g || !q_inout || !copts) return invalid("null argument");
   const fv_critical_opts c = *copts;
-  if (!(c.gr_a > 0.0) || !(c.gr_b > 0.0) || c.gr_a == c.gr_b || !(c.tol > 0.0) || c.max_iter < 0 ||
-      c.max_iter > 38 || c.mode < FV_MODE_LEADING || c.mode > FV_MODE_OSCILLATORY || k < 1 || k > 62)
+  if (!critical_opts_ok(c) || c.mode < FV_MODE_LEADING || c.mode > FV_MODE_OSCILLATORY || k < 1 || k > 62)
     return invalid("bad critical-Gr options (need distinct gr_a, gr_b > 0, tol > 0, 0 <= max_iter <= 38)");
   fv_newton_opts no;
   if (nopts)
@@ -2511,9 +2607,6 @@ extern "C" int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton
     ao = *aopts;
   else
     fv_arnoldi_default_opts(&ao);
-  fv_critical_report rep;
-  std::memset(&rep, 0, sizeof(rep));
-  rep.status = FV_ENOCONV;
   const size_t n = 4 * g->N;
   // states of the evaluations so far: a Newton start for the next Gr is the one of the nearest Gr
   std::vector<DevBuf<double>> states(c.max_iter + 2);
@@ -2546,81 +2639,26 @@ extern "C" int fv_critical_gr(fv_grid g, int k, double* q_inout, const fv_newton
       return FV_ENOCONV;
     }
     grs.push_back(gr);
-    if (rep.evaluations < 40) {
-      rep.gr[rep.evaluations] = gr;
-      rep.re[rep.evaluations] = *lr;
-      rep.im[rep.evaluations] = *li;
-    }
-    ++rep.evaluations;
     return FV_OK;
   };
-  double fa, ia, fb, ib;
-  double a = c.gr_a, b = c.gr_b;
-  int st = evaluate(a, &fa, &ia);
-  if (st == FV_OK) st = evaluate(b, &fb, &ib);
-  int side = 0;  // Illinois: which end was kept last time (-1: a, +1: b)
-  bool bracketed = st == FV_OK && fa * fb <= 0.0;
-  double x = b, fx = fb, ix = ib;
-  for (int it = 0; st == FV_OK && it < c.max_iter; ++it) {
-    if (fb == fa) break;
-    double xn = b - fb * (b - a) / (fb - fa);
-    if (!bracketed) {  // secant: keep the step within twice the current spacing
-      const double lim = 2.0 * std::fabs(b - a);
-      xn = std::min(std::max(xn, b - lim), b + lim);
-    }
-    if (!(xn > 0.0)) xn = 0.5 * std::min(a, b);
-    double fn, in;
-    st = evaluate(xn, &fn, &in);
-    if (st != FV_OK) break;
-    x = xn;
-    fx = fn;
-    ix = in;
-    const bool done = std::fabs(xn - b) <= c.tol * std::fabs(b) || fn == 0.0;
-    // b is always the newest point; once a sign change is seen, a and b keep opposite signs
-    if (!bracketed && fn * fa < 0.0 && fn * fb > 0.0) {
-      bracketed = true;  // the crossing lies between a and xn: keep a
-      b = xn;
-      fb = fn;
-    } else if (!bracketed && fn * fb < 0.0) {
-      bracketed = true;  // between b and xn
-      a = b;
-      fa = fb;
-      b = xn;
-      fb = fn;
-      side = 0;
-    } else if (!bracketed) {  // secant step
-      a = b;
-      fa = fb;
-      b = xn;
-      fb = fn;
-    } else if (fn * fb < 0.0) {  // false position: the newest end changed sign, the old b becomes a
-      a = b;
-      fa = fb;
-      b = xn;
-      fb = fn;
-      side = 0;
-    } else {  // a is retained again: Illinois halves its value so that it is not retained forever
-      if (side == -1) fa *= 0.5;
-      side = -1;
-      b = xn;
-      fb = fn;
-    }
-    if (done) {
-      rep.status = FV_OK;
-      break;
-    }
-  }
-  if (rep.evaluations > 0) {
-    rep.gr_cr = x;
-    rep.lam_re = fx;
-    rep.lam_im = ix;
-    rep.omega_scaled = ix / std::sqrt(x);
-    // the steady state of the last evaluation
-    FV_CUDA(cudaMemcpyAsync(q_inout, states[grs.size() - 1].p, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+  fv_critical_report rep;
+  critical_root(c, evaluate, &rep);
+  if (rep.evaluations > 0) {  // the steady state of the last successful evaluation
+    FV_CUDA(cudaMemcpyAsync(q_inout, states[rep.evaluations - 1].p, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                             g->stream));
     FV_CUDA(cudaStreamSynchronize(g->stream));
   }
-  if (st != FV_OK) rep.status = st;
+  if (report) *report = rep;
+  return rep.status;
+}
+
+extern "C" int fv_critical_root(const fv_critical_opts* copts, fv_tracked_fn f, void* ctx,
+                                fv_critical_report* report) {
+  if (!copts || !f) return invalid("null argument");
+  if (!critical_opts_ok(*copts))
+    return invalid("bad critical-Gr options (need distinct gr_a, gr_b > 0, tol > 0, 0 <= max_iter <= 38)");
+  fv_critical_report rep;
+  critical_root(*copts, [&](double gr, double* lr, double* li) -> int { return f(gr, ctx, lr, li); }, &rep);
   if (report) *report = rep;
   return rep.status;
 }

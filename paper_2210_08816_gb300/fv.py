@@ -71,6 +71,9 @@ class fv_critical_report(C.Structure):
 
 FV_MODE_LEADING, FV_MODE_REAL, FV_MODE_OSCILLATORY = 0, 1, 2
 
+# int (*fv_tracked_fn)(double gr, void* ctx, double* re, double* im)
+TRACKED_FN = C.CFUNCTYPE(C.c_int, C.c_double, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double))
+
 _lib = None
 
 
@@ -117,6 +120,7 @@ def lib():
             "fv_critical_default_opts": (None, [C.POINTER(fv_critical_opts)]),
             "fv_critical_gr": (i, [vp, i, vp, C.POINTER(fv_newton_opts), C.POINTER(fv_arnoldi_opts),
                                    C.POINTER(fv_critical_opts), C.POINTER(fv_critical_report)]),
+            "fv_critical_root": (i, [C.POINTER(fv_critical_opts), TRACKED_FN, vp, C.POINTER(fv_critical_report)]),
             "fv_richardson": (i, [i, C.POINTER(d), C.POINTER(d), C.POINTER(d), C.POINTER(d)]),
             "fv_profile": (i, [vp, i]),
             "fv_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong)]),
@@ -136,7 +140,7 @@ EXPORTED = ["fv_grid_create", "fv_grid_destroy", "fv_set_stream", "fv_state_elem
             "fv_project", "fv_jvp_project", "fv_jvp_project_lincomb", "fv_jvp_project_lincomb_dev", "fv_dot",
             "fv_dot_noalloc", "fv_axpby", "fv_convert", "fv_diffusion_solve", "fv_jvp_project_batch",
             "fv_get_tuning", "fv_transfer", "fv_diagnostics", "fv_time_step", "fv_batch_plan_create", "fv_batch_plan_launch", "fv_batch_plan_destroy",
-            "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_critical_default_opts", "fv_critical_gr", "fv_richardson", "fv_profile",
+            "fv_newton_default_opts", "newton_steady", "fv_arnoldi_default_opts", "arnoldi_leading", "fv_critical_default_opts", "fv_critical_gr", "fv_critical_root", "fv_richardson", "fv_profile",
             "fv_profile_read", "fv_strerror", "fv_last_error"]
 
 FV_PROF_CLASSES = 7
@@ -478,6 +482,30 @@ def fv_critical_gr(g: Grid, k, q, copts: fv_critical_opts, nopts: fv_newton_opts
     st = lib().fv_critical_gr(g.h, int(k), _ptr(q, torch.float64, g.n, "q"), C.byref(nopts) if nopts else None,
                               C.byref(aopts) if aopts else None, C.byref(copts), C.byref(rep))
     _check(st, "fv_critical_gr", ok=(FV_OK, FV_ENOCONV))
+    return st, rep
+
+
+def fv_critical_root(copts: fv_critical_opts, f):
+    """The root iteration of fv_critical_gr on a host function f(gr) -> the tracked eigenvalue (complex or
+    real).  Returns (status, report); FV_ENOCONV is returned, not raised; an exception raised by f ends the
+    iteration and is raised again here."""
+    raised = []
+
+    def tracked(gr, ctx, re, im):
+        try:
+            lam = complex(f(gr))
+        except Exception as e:  # noqa: BLE001 -- raised again after the call returns
+            raised.append(e)
+            return FV_EINVAL
+        re[0], im[0] = lam.real, lam.imag
+        return FV_OK
+
+    cb = TRACKED_FN(tracked)
+    rep = fv_critical_report()
+    st = lib().fv_critical_root(C.byref(copts), cb, None, C.byref(rep))
+    if raised:
+        raise raised[0]
+    _check(st, "fv_critical_root", ok=(FV_OK, FV_ENOCONV))
     return st, rep
 
 
