@@ -1,0 +1,62 @@
+// Test-only C wrappers of the library's host linear algebra (paper_2210_08816_gb300/csrc/host_linalg.cpp),
+// compiled together with it by tests/test_host_linalg.py into a temporary shared object so that the
+// routines the eigen-solver and the pressure solve rely on can be checked on the CPU.  Matrices are
+// row-major double arrays; every wrapper copies in and out of the routines' std::vector arguments.
+#include <cstring>
+#include <vector>
+
+#include "fv_internal.h"
+
+extern "C" {
+
+// d (n, in: diagonal, out: eigenvalues), e (n - 1), Q (n * n, column j = eigenvector j)
+int shim_tridiag_eig(int n, double* d, const double* e, double* Q) {
+  std::vector<double> dv(d, d + n), ev(n > 1 ? n - 1 : 1, 0.0), Qv;
+  if (n > 1) std::memcpy(ev.data(), e, sizeof(double) * (n - 1));
+  const bool ok = fv::tridiag_eig(n, dv, ev, Qv);
+  std::memcpy(d, dv.data(), sizeof(double) * n);
+  std::memcpy(Q, Qv.data(), sizeof(double) * n * n);
+  return ok ? 1 : 0;
+}
+
+int shim_hessenberg_eigvals(int m, const double* H, double* re, double* im) {
+  std::vector<double> r, i;
+  const bool ok = fv::hessenberg_eigvals(m, H, m, r, i);
+  if (ok) {
+    std::memcpy(re, r.data(), sizeof(double) * m);
+    std::memcpy(im, i.data(), sizeof(double) * m);
+  }
+  return ok ? 1 : 0;
+}
+
+// y: 2 m doubles, (re, im) interleaved
+int shim_hessenberg_eigvec(int m, const double* H, double lre, double lim, double* y) {
+  std::vector<double> yv;
+  const bool ok = fv::hessenberg_eigvec(m, H, m, lre, lim, yv);
+  if (ok) std::memcpy(y, yv.data(), sizeof(double) * 2 * m);
+  return ok ? 1 : 0;
+}
+
+// A (m * m, in: general, out: Hessenberg H), Q (m * m) with A_in = Q H Q^T
+void shim_hessenberg_reduce(int m, double* A, double* Q) {
+  std::vector<double> Av(A, A + (size_t)m * m), Qv;
+  fv::hessenberg_reduce(m, Av, Qv);
+  std::memcpy(A, Av.data(), sizeof(double) * m * m);
+  std::memcpy(Q, Qv.data(), sizeof(double) * m * m);
+}
+
+// H: (j + 1) x j with leading dimension ld; y: j
+void shim_hessenberg_lstsq(int j, const double* H, int ld, double beta, double* y, double* resid) {
+  std::vector<double> yv;
+  fv::hessenberg_lstsq(j, H, ld, beta, yv, resid);
+  std::memcpy(y, yv.data(), sizeof(double) * j);
+}
+
+int shim_dense_solve(int n, const double* A, double* b) {
+  std::vector<double> Av(A, A + (size_t)n * n), bv(b, b + n);
+  const bool ok = fv::dense_solve(n, Av, bv);
+  if (ok) std::memcpy(b, bv.data(), sizeof(double) * n);
+  return ok ? 1 : 0;
+}
+
+}  // extern "C"
