@@ -269,6 +269,21 @@ bool dense_solve(int n, std::vector<double> A, std::vector<double>& b);
 // Least squares min || H y - beta e1 || for the (j+1) x j Hessenberg of GMRES (row-major, ld).
 void hessenberg_lstsq(int j, const double* H, int ld, double beta, std::vector<double>& y, double* resid);
 
+// ------------------------------------------------------------------ Chebyshev filter ellipses (host_cheb.cpp)
+struct Ritz {
+  double re, im;
+};
+// Level |w| of z = zr + i zi in the confocal family with foci d +- c (c^2 = c2 real, possibly negative;
+// c2 = 0: circles about d): z - d = c (w + 1/w) / 2, the branch |w| >= 1.
+double ellipse_level(double zr, double zi, double d, double c2);
+// Rightmost real point of the ellipse of the given level in that family.
+double ellipse_right_end(double d, double c2, double level);
+// Scan of real-centred confocal ellipses for the one maximising min over wanted of the level divided by
+// max over unwanted of the level, among those whose right end stays left of every wanted real part (the
+// best of all if none does); rate_out = that ratio.
+void best_ellipse(const std::vector<Ritz>& wanted, const std::vector<Ritz>& unwanted, double& d_out,
+                  double& c2_out, double& rate_out);
+
 // ------------------------------------------------------------------ drivers (fv_api.cpp)
 template <typename R>
 int jvp_project(fv_grid_s* g, double Gr, double sigma, const R* q, const R* v, R* out);

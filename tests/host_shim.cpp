@@ -1,7 +1,8 @@
-// Test-only C wrappers of the library's host linear algebra (paper_2210_08816_gb300/csrc/host_linalg.cpp),
-// compiled together with it by tests/test_host_linalg.py into a temporary shared object so that the
-// routines the eigen-solver and the pressure solve rely on can be checked on the CPU.  Matrices are
-// row-major double arrays; every wrapper copies in and out of the routines' std::vector arguments.
+// Test-only C wrappers of the library's host-only code (paper_2210_08816_gb300/csrc/host_linalg.cpp and
+// host_cheb.cpp), compiled together with those sources by the `host_shim` fixture of tests/conftest.py into
+// a temporary shared object, so that the routines the eigen-solvers and the pressure solve rely on can be
+// checked on the CPU.  Matrices are row-major double arrays; every wrapper copies in and out of the
+// routines' std::vector arguments.
 #include <cstring>
 #include <vector>
 
@@ -57,6 +58,18 @@ int shim_dense_solve(int n, const double* A, double* b) {
   const bool ok = fv::dense_solve(n, Av, bv);
   if (ok) std::memcpy(b, bv.data(), sizeof(double) * n);
   return ok ? 1 : 0;
+}
+
+double shim_ellipse_level(double zr, double zi, double d, double c2) { return fv::ellipse_level(zr, zi, d, c2); }
+
+double shim_ellipse_right_end(double d, double c2, double level) { return fv::ellipse_right_end(d, c2, level); }
+
+void shim_best_ellipse(int nw, const double* wre, const double* wim, int nu, const double* ure, const double* uim,
+                       double* d, double* c2, double* rate) {
+  std::vector<fv::Ritz> w(nw), u(nu);
+  for (int i = 0; i < nw; ++i) w[i] = {wre[i], wim[i]};
+  for (int i = 0; i < nu; ++i) u[i] = {ure[i], uim[i]};
+  fv::best_ellipse(w, u, *d, *c2, *rate);
 }
 
 }  // extern "C"

@@ -3,33 +3,23 @@
 These routines carry the pressure solve's 1D eigen-decompositions (symmetric tridiagonal QR), the Arnoldi
 iteration's Hessenberg eigenproblem and Ritz vectors (Section 1 methods paragraph, Section 3), the Rayleigh-
 Ritz reduction, BiCGstab(2)'s small systems and GMRES's least-squares problem.  They are compiled here with
-a test-only C wrapper (tests/host_linalg_shim.cpp) and checked against what fixes them independently:
+a test-only C wrapper (tests/host_shim.cpp) and checked against what fixes them independently:
 matrices built with a known spectrum (orthogonal similarity of a block-diagonal matrix), the defining
 identities (T Q = Q Lambda, Q^T Q = I, A = Q H Q^T, H y = lambda y), and SciPy / NumPy's LAPACK routines.
 """
 import ctypes as C
-import os
-import subprocess
 
 import numpy as np
 import pytest
 
 sl = pytest.importorskip("scipy.linalg")
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2210_08816_gb300", "csrc")
 DP = C.POINTER(C.c_double)
 
 
 @pytest.fixture(scope="module")
-def L(tmp_path_factory):
-    out = tmp_path_factory.mktemp("hostlinalg") / "libhostlinalg.so"
-    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
-    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-I{cuda}/include", f"-I{CSRC}",
-           os.path.join(ROOT, "tests", "host_linalg_shim.cpp"), os.path.join(CSRC, "host_linalg.cpp"), "-o", str(out)]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
-    lib = C.CDLL(str(out))
+def L(host_shim):
+    lib = host_shim
     i = C.c_int
     for name, res, args in [("shim_tridiag_eig", i, [i, DP, DP, DP]),
                             ("shim_hessenberg_eigvals", i, [i, DP, DP, DP]),
