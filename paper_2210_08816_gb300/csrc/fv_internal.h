@@ -269,6 +269,24 @@ bool dense_solve(int n, std::vector<double> A, std::vector<double>& b);
 // Least squares min || H y - beta e1 || for the (j+1) x j Hessenberg of GMRES (row-major, ld).
 void hessenberg_lstsq(int j, const double* H, int ld, double beta, std::vector<double>& y, double* resid);
 
+// ------------------------------------------------------------------ grid axes (host_grid.cpp)
+// One axis of the grid, FP64 on the host.  idx[c] = 1 / width of cell c; idc[f] = 1 / centre spacing across
+// face f (idc[0] = 2 / width[0], idc[n] = 2 / width[n-1]); wl[f], wr[f] = interpolation weights of cells
+// f-1 and f at face f; lam, Einv, E: the Neumann operator L = E diag(lam) Einv (modes by decreasing
+// eigenvalue, lam[0] = 0 the constant vector); n x n matrices row-major.
+struct AxisHost {
+  int n;
+  std::vector<double> idx, idc, wl, wr, lam, Einv, E;
+  // diffusion operators of the Newton preconditioner: cell-centred with Dirichlet walls half a cell away
+  // (transverse velocities, T along x) and face-centred with Dirichlet walls (a velocity along its own
+  // axis; mode 0 is a dummy that maps the wall slot 0 to itself)
+  std::vector<double> cd_lam, cd_Einv, cd_E, fd_lam, fd_Einv, fd_E;
+};
+// Faces 0 .. n of the tanh-stretched grid with stretching s (s = 0: uniform), mirrored about 1/2.
+std::vector<double> tanh_faces(int n, double s);
+// Metrics and 1D decompositions of the axis with faces xf (strictly increasing); FV_EINVAL otherwise.
+int build_axis(const std::vector<double>& xf, AxisHost& a);
+
 // ------------------------------------------------------------------ Chebyshev filter ellipses (host_cheb.cpp)
 struct Ritz {
   double re, im;

@@ -1,12 +1,18 @@
-// Test-only C wrappers of the library's host-only code (paper_2210_08816_gb300/csrc/host_linalg.cpp and
-// host_cheb.cpp), compiled together with those sources by the `host_shim` fixture of tests/conftest.py into
+// Test-only C wrappers of the library's host-only code (paper_2210_08816_gb300/csrc/host_linalg.cpp,
+// host_cheb.cpp and host_grid.cpp), compiled together with those sources by the `host_shim` fixture of tests/conftest.py into
 // a temporary shared object, so that the routines the eigen-solvers and the pressure solve rely on can be
 // checked on the CPU.  Matrices are row-major double arrays; every wrapper copies in and out of the
 // routines' std::vector arguments.
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "fv_internal.h"
+
+// The library's error-message sink lives in its driver unit, which this object does not include.
+namespace fv {
+void set_error(const std::string&) {}
+}  // namespace fv
 
 extern "C" {
 
@@ -70,6 +76,36 @@ void shim_best_ellipse(int nw, const double* wre, const double* wim, int nu, con
   for (int i = 0; i < nw; ++i) w[i] = {wre[i], wim[i]};
   for (int i = 0; i < nu; ++i) u[i] = {ure[i], uim[i]};
   fv::best_ellipse(w, u, *d, *c2, *rate);
+}
+
+void shim_tanh_faces(int n, double s, double* f) {
+  const std::vector<double> v = fv::tanh_faces(n, s);
+  std::memcpy(f, v.data(), sizeof(double) * (n + 1));
+}
+
+// xf: n + 1 faces; outputs: idx, idc, wl, wr (n + 1 each), lam, cd_lam, fd_lam (n), and the n x n
+// matrices Einv, E, cd_Einv, cd_E, fd_Einv, fd_E
+int shim_build_axis(int n, const double* xf, double* idx, double* idc, double* wl, double* wr, double* lam,
+                    double* Einv, double* E, double* cd_lam, double* cd_Einv, double* cd_E, double* fd_lam,
+                    double* fd_Einv, double* fd_E) {
+  fv::AxisHost a;
+  const int st = fv::build_axis(std::vector<double>(xf, xf + n + 1), a);
+  if (st != FV_OK) return st;
+  auto put = [](double* dst, const std::vector<double>& v) { std::memcpy(dst, v.data(), sizeof(double) * v.size()); };
+  put(idx, a.idx);
+  put(idc, a.idc);
+  put(wl, a.wl);
+  put(wr, a.wr);
+  put(lam, a.lam);
+  put(Einv, a.Einv);
+  put(E, a.E);
+  put(cd_lam, a.cd_lam);
+  put(cd_Einv, a.cd_Einv);
+  put(cd_E, a.cd_E);
+  put(fd_lam, a.fd_lam);
+  put(fd_Einv, a.fd_Einv);
+  put(fd_E, a.fd_E);
+  return FV_OK;
 }
 
 }  // extern "C"
