@@ -18,7 +18,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libcubefv.so")
 SOURCES = ["kernels_stencil.cu", "kernels_stencil2.cu", "kernels_fdm.cu", "kernels_tc.cu", "kernels_blas.cu", "host_linalg.cpp",
-           "host_cheb.cpp", "host_grid.cpp", "fv_api.cpp", "noalloc.cu", "kernels_prolong.cu", "kernels_diag.cu"]
+           "host_cheb.cpp", "host_grid.cpp", "host_tc.cpp", "fv_api.cpp", "noalloc.cu", "kernels_prolong.cu", "kernels_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -269,6 +269,21 @@ bool dense_solve(int n, std::vector<double> A, std::vector<double>& b);
 // Least squares min || H y - beta e1 || for the (j+1) x j Hessenberg of GMRES (row-major, ld).
 void hessenberg_lstsq(int j, const double* H, int ld, double beta, std::vector<double>& y, double* resid);
 
+// ------------------------------------------------------------------ tensor-core operands (host_tc.cpp)
+constexpr int kTcSlabCols = 16;  // FP32 K columns per slab of the tensor-core passes (one 64-byte row)
+// One float buffer: per axis [fwd_s_hi, fwd_s_lo, fwd_a_hi, fwd_a_lo, bwd_s_hi, bwd_s_lo, bwd_a_hi,
+// bwd_a_lo] (h x h each, at moff), the eigenvalues in the tensor-core mode order (n, at loff), and per
+// axis and direction the swizzled per-step B blocks of the persistent pass (4 h^2, at soff, 256-byte
+// aligned); offsets in floats.
+struct TcOperands {
+  std::vector<float> buf;
+  size_t moff[3][8], loff[3], soff[3][2];
+};
+// Builds the operands for axes of ns[d] cells (even, ns[d] / 2 a multiple of kTcSlabCols) from the
+// metric arrays idx (1 / widths) and idc (1 / centre spacings) of each axis.  FV_EINVAL on failure.
+int tc_host_operands(const int ns[3], const std::vector<double>* idx, const std::vector<double>* idc,
+                     TcOperands& out);
+
 // ------------------------------------------------------------------ grid axes (host_grid.cpp)
 // One axis of the grid, FP64 on the host.  idx[c] = 1 / width of cell c; idc[f] = 1 / centre spacing across
 // face f (idc[0] = 2 / width[0], idc[n] = 2 / width[n-1]); wl[f], wr[f] = interpolation weights of cells

@@ -17,14 +17,16 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def host_shim(tmp_path_factory):
-    """The library's host-only sources (linear algebra, Chebyshev-filter ellipses, grid axes) with the test-only
-    C wrappers of tests/host_shim.cpp, compiled by g++ into a temporary shared object (no CUDA runtime)."""
+    """The library's host-only sources (linear algebra, Chebyshev-filter ellipses, grid axes, tensor-core
+    operands) with the test-only C wrappers of tests/host_shim.cpp, compiled by g++ into a temporary
+    shared object (no CUDA runtime)."""
     out = tmp_path_factory.mktemp("hostshim") / "libhostshim.so"
     csrc = os.path.join(ROOT, "paper_2210_08816_gb300", "csrc")
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-I{cuda}/include", f"-I{csrc}",
            os.path.join(ROOT, "tests", "host_shim.cpp"), os.path.join(csrc, "host_linalg.cpp"),
-           os.path.join(csrc, "host_cheb.cpp"), os.path.join(csrc, "host_grid.cpp"), "-o", str(out)]
+           os.path.join(csrc, "host_cheb.cpp"), os.path.join(csrc, "host_grid.cpp"),
+           os.path.join(csrc, "host_tc.cpp"), "-o", str(out)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return ctypes.CDLL(str(out))

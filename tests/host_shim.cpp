@@ -1,5 +1,5 @@
 // Test-only C wrappers of the library's host-only code (paper_2210_08816_gb300/csrc/host_linalg.cpp,
-// host_cheb.cpp and host_grid.cpp), compiled together with those sources by the `host_shim` fixture of tests/conftest.py into
+// host_cheb.cpp, host_grid.cpp and host_tc.cpp), compiled together with those sources by the `host_shim` fixture of tests/conftest.py into
 // a temporary shared object, so that the routines the eigen-solvers and the pressure solve rely on can be
 // checked on the CPU.  Matrices are row-major double arrays; every wrapper copies in and out of the
 // routines' std::vector arguments.
@@ -106,6 +106,35 @@ int shim_build_axis(int n, const double* xf, double* idx, double* idc, double* w
   put(fd_Einv, a.fd_Einv);
   put(fd_E, a.fd_E);
   return FV_OK;
+}
+
+// Tensor-core operands of an nx x ny x nz grid with tanh stretching s (the library's faces and metrics).
+// buf == NULL: returns the buffer length in floats.  Otherwise fills buf (cap floats), moff (24), loff (3)
+// and soff (6) and returns the length; a negative value is the library's status.
+long long shim_tc_operands(int nx, int ny, int nz, double s, float* buf, long long cap, long long* moff,
+                           long long* loff, long long* soff) {
+  const int ns[3] = {nx, ny, nz};
+  std::vector<double> idx[3], idc[3];
+  for (int d = 0; d < 3; ++d) {
+    fv::AxisHost a;
+    const int st = fv::build_axis(fv::tanh_faces(ns[d], s), a);
+    if (st != FV_OK) return st;
+    idx[d] = a.idx;
+    idc[d] = a.idc;
+  }
+  fv::TcOperands op;
+  const int st = fv::tc_host_operands(ns, idx, idc, op);
+  if (st != FV_OK) return st;
+  const long long len = (long long)op.buf.size();
+  if (!buf) return len;
+  if (cap < len) return FV_EINVAL;
+  std::memcpy(buf, op.buf.data(), sizeof(float) * op.buf.size());
+  for (int d = 0; d < 3; ++d) {
+    for (int j = 0; j < 8; ++j) moff[d * 8 + j] = (long long)op.moff[d][j];
+    loff[d] = (long long)op.loff[d];
+    for (int dir = 0; dir < 2; ++dir) soff[d * 2 + dir] = (long long)op.soff[d][dir];
+  }
+  return len;
 }
 
 }  // extern "C"
