@@ -4,6 +4,8 @@
   beside each field ("(default X)" or "X (default)"): the header is the user's only statement of them.
 * The binding refuses what the library could not dereference (host tensors, wrong dtype or size) before
   any call reaches the device, with FvError(FV_EINVAL).
+* fv_grid_create refuses sizes outside [2, 1024] per axis or with 4 N >= 2^31, a non-positive Pr, and
+  caller faces that do not run strictly increasing from 0 to 1, before any device allocation.
 """
 import os
 import re
@@ -69,3 +71,27 @@ def test_status_strings_cover_every_code(fv):
     texts = {c: L.fv_strerror(c).decode() for c in codes}
     assert all(texts.values()), texts
     assert len(set(texts.values())) == len(codes), texts
+
+
+@pytest.mark.parametrize("nx,ny,nz,Pr", [(1, 8, 8, 0.71), (8, 1025, 8, 0.71), (8, 8, 8, 0.0), (8, 8, 8, -1.0),
+                                         (1024, 1024, 1024, 0.71)])
+def test_grid_create_refuses_bad_sizes(fv, nx, ny, nz, Pr):
+    import ctypes as C
+    desc = fv.fv_grid_desc(nx=nx, ny=ny, nz=nz, stretch=1.5, Pr=Pr)
+    h = C.c_void_p()
+    assert fv.lib().fv_grid_create(C.byref(desc), None, C.byref(h)) == fv.FV_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("faces", [[0.1, 0.5, 1.0], [0.0, 0.5, 0.9], [0.0, 0.5, 0.5, 1.0], [0.0, 0.7, 0.4, 1.0]])
+def test_grid_create_refuses_bad_faces(fv, faces):
+    import ctypes as C
+    n = len(faces) - 1
+    arr = (C.c_double * len(faces))(*faces)
+    ok = (C.c_double * (n + 1))(*[i / n for i in range(n + 1)])
+    desc = fv.fv_grid_desc(nx=n, ny=n, nz=n, stretch=0.0, Pr=0.71)
+    desc.xf = C.cast(arr, C.POINTER(C.c_double))
+    desc.yf = desc.zf = C.cast(ok, C.POINTER(C.c_double))
+    h = C.c_void_p()
+    assert fv.lib().fv_grid_create(C.byref(desc), None, C.byref(h)) == fv.FV_EINVAL
+    assert not h.value
