@@ -73,6 +73,9 @@ typedef struct {
 
 /* Create a grid handle: metric arrays, the 1D generalised eigen-decompositions
  * used by the pressure solve (computed on the host in FP64), and workspace.
+ * The FP32 pressure solve runs on the tensor cores when every axis has 32 to 256
+ * cells, a multiple of 32, and faces mirror-symmetric about 1/2 (as the built-in
+ * grids are); other grids take the CUDA-core passes, with the same results.
  * `stream` is a cudaStream_t (NULL = legacy default stream).
  * Errors: FV_EINVAL (sizes, faces), FV_ENOMEM, FV_ECUDA. */
 int fv_grid_create(const fv_grid_desc* desc, void* stream, fv_grid* out);

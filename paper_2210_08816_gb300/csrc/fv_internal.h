@@ -301,6 +301,10 @@ struct AxisHost {
 std::vector<double> tanh_faces(int n, double s);
 // Metrics and 1D decompositions of the axis with faces xf (strictly increasing); FV_EINVAL otherwise.
 int build_axis(const std::vector<double>& xf, AxisHost& a);
+// True if the faces are their own mirror image about 1/2 (x_f[n-i] = 1 - x_f[i] to 4 units of round-off):
+// the tensor-core passes split each 1D eigenproblem into symmetric and antisymmetric halves, which holds
+// only on such axes.
+bool mirror_symmetric(const std::vector<double>& xf);
 
 // ------------------------------------------------------------------ Chebyshev filter ellipses (host_cheb.cpp)
 struct Ritz {

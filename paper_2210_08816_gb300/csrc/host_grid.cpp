@@ -5,6 +5,7 @@
 // preconditioner's diffusion solves (Dirichlet, cell- and face-centred).
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -20,6 +21,14 @@ int invalid(const std::string& msg) {
 }
 
 }  // namespace
+
+bool mirror_symmetric(const std::vector<double>& xf) {
+  const int n = (int)xf.size() - 1;
+  const double tol = 4.0 * std::numeric_limits<double>::epsilon();
+  for (int i = 0; i <= n; ++i)
+    if (std::fabs(xf[n - i] - (1.0 - xf[i])) > tol) return false;
+  return true;
+}
 
 std::vector<double> tanh_faces(int n, double s) {
   std::vector<double> f(n + 1);

@@ -679,8 +679,10 @@ size_t tcp_smem_bytes(int n) {
 
 bool tc_eligible(const fv_grid_s* g) {
   const int ns[3] = {g->nx, g->ny, g->nz};
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
     if (ns[d] < 32 || ns[d] > 256 || ns[d] % 32 != 0) return false;
+    if (!mirror_symmetric(g->xf[d])) return false;  // the half-size eigenproblems need a symmetric axis
+  }
   return encoder() != nullptr;
 }
 

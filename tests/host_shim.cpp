@@ -83,6 +83,10 @@ void shim_tanh_faces(int n, double s, double* f) {
   std::memcpy(f, v.data(), sizeof(double) * (n + 1));
 }
 
+int shim_mirror_symmetric(int n, const double* xf) {
+  return fv::mirror_symmetric(std::vector<double>(xf, xf + n + 1)) ? 1 : 0;
+}
+
 // xf: n + 1 faces; outputs: idx, idc, wl, wr (n + 1 each), lam, cd_lam, fd_lam (n), and the n x n
 // matrices Einv, E, cd_Einv, cd_E, fd_Einv, fd_E
 int shim_build_axis(int n, const double* xf, double* idx, double* idc, double* wl, double* wr, double* lam,

@@ -131,3 +131,25 @@ def test_uniform_grid_takes_the_textbook_eigenvalues(L, n):
 def test_non_increasing_faces_are_refused(L):
     st, _ = _axis(L, np.array([0.0, 0.5, 0.5, 1.0]))
     assert st != 0
+
+
+def test_only_mirror_symmetric_axes_take_the_tensor_core_passes(L):
+    # the tensor-core passes split every 1D eigenproblem into symmetric and antisymmetric halves: an axis
+    # qualifies only if its faces are their own mirror image about 1/2
+    f = L.shim_mirror_symmetric
+    f.restype, f.argtypes = C.c_int, [C.c_int, DP]
+
+    def sym(x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        return f(len(x) - 1, x.ctypes.data_as(DP)) == 1
+
+    for n, s in [(32, 0.0), (64, 1.5), (256, 1.5), (33, 2.0)]:
+        assert sym(_faces(L, n, s))
+    one_sided = (np.exp(2.0 * np.arange(65) / 64) - 1.0) / (np.exp(2.0) - 1.0)  # clustered at x = 0 only
+    assert not sym(one_sided)
+    x = _faces(L, 64, 1.5)
+    x[10] += 1e-9
+    assert not sym(x)
+    x = _faces(L, 64, 1.5)
+    x[10] = np.nextafter(x[10], 1.0)  # one unit of round-off stays within the tolerance
+    assert sym(x)
