@@ -49,11 +49,16 @@ def faces(n: int, stretch: float) -> np.ndarray:
 
 
 class Axis:
-    """Metric arrays of one axis with n cells."""
+    """Metric arrays of one axis with n cells (faces from `faces(n, stretch)`, or the given xf)."""
 
-    def __init__(self, n: int, stretch: float):
+    def __init__(self, n: int, stretch: float, xf=None):
         self.n = n
-        self.xf = faces(n, stretch)
+        if xf is None:
+            self.xf = faces(n, stretch)
+        else:
+            self.xf = np.array(xf, dtype=np.float64)
+            if self.xf.shape != (n + 1,) or self.xf[0] != 0.0 or self.xf[-1] != 1.0 or np.any(np.diff(self.xf) <= 0):
+                raise ValueError("faces must be n + 1 strictly increasing values from 0 to 1")
         self.dx = np.diff(self.xf)                      # cell widths, n
         self.xc = 0.5 * (self.xf[:-1] + self.xf[1:])    # cell centres (face midpoints), n
         self.dc = np.diff(self.xc)                      # centre spacing across interior face i = 1..n-1, n-1
@@ -64,10 +69,12 @@ class Axis:
 
 
 class Grid:
-    """Tensor-product grid of the unit cube; axes[0] = x, axes[1] = y, axes[2] = z."""
+    """Tensor-product grid of the unit cube; axes[0] = x, axes[1] = y, axes[2] = z.  xyz_faces: optional
+    (xf, yf, zf), each None (the stretch law) or the n + 1 faces of that axis."""
 
-    def __init__(self, nx: int, ny: int, nz: int, stretch: float = 0.0, Pr: float = 0.71):
-        self.axes = [Axis(nx, stretch), Axis(ny, stretch), Axis(nz, stretch)]
+    def __init__(self, nx: int, ny: int, nz: int, stretch: float = 0.0, Pr: float = 0.71, xyz_faces=None):
+        f = xyz_faces if xyz_faces is not None else (None, None, None)
+        self.axes = [Axis(nx, stretch, f[0]), Axis(ny, stretch, f[1]), Axis(nz, stretch, f[2])]
         self.nx, self.ny, self.nz = nx, ny, nz
         self.Pr = Pr
 

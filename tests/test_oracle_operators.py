@@ -9,7 +9,8 @@
 * Closed-form eigenvectors of the diffusion part with the wall closures of
   Section 2 (no-slip; Eq. 4 Dirichlet; Eqs. 5-6 Neumann).
 * F is quadratic, so central differences of F reproduce J.v exactly.
-* The three symmetries of Section 2 commute with P F and with J.
+* The three symmetries of Section 2 commute with P F and with J; on a grid without mirror symmetry the
+  reflection y -> 1 - y maps F and J.v on the grid to F and J.v on the reflected grid.
 """
 import numpy as np
 import pytest
@@ -101,13 +102,25 @@ def _sample(g, fns):
     return out
 
 
-@pytest.mark.parametrize("stretch", [0.0, 1.5])
+def _one_sided(n, a):
+    """Faces clustered towards x = 0 only (no mirror symmetry): x_f = (e^(a i/n) - 1) / (e^a - 1)."""
+    xf = np.expm1(a * np.arange(n + 1) / n) / np.expm1(a)
+    xf[0], xf[-1] = 0.0, 1.0
+    return xf
+
+
+@pytest.mark.parametrize("stretch", [0.0, 1.5, "one-sided"])
 def test_residual_second_order_against_pde(stretch):
+    # the one-sided grid has no mirror symmetry, so a metric index taken from the wrong end of an axis
+    # (which a mirror-symmetric grid cannot show) breaks the convergence
     Gr = 40.0
     fields, exact = _mms_functions(Gr)
     errs = []
     for n in (16, 32, 64):
-        g = D.Grid(n, n, n, stretch=stretch, Pr=PR)
+        if stretch == "one-sided":
+            g = D.Grid(n, n, n, Pr=PR, xyz_faces=(_one_sided(n, 1.2), _one_sided(n, -0.8), _one_sided(n, 0.6)))
+        else:
+            g = D.Grid(n, n, n, stretch=stretch, Pr=PR)
         q = _sample(g, fields)
         for c in range(3):                       # no-slip: the sampled walls are ~1e-16; make them exact
             ax = 2 - c
@@ -126,7 +139,10 @@ def test_residual_second_order_against_pde(stretch):
     errs = np.array(errs)
     assert np.all(errs[-1] < 5e-3)
     ratios = errs[:-1] / errs[1:]
-    assert np.all(ratios > 3.0), (errs, ratios)
+    if stretch == "one-sided":   # the place of the largest error moves between levels: judge two halvings
+        assert np.all(ratios > 2.5) and np.all(errs[0] / errs[-1] > 10.0), (errs, ratios)
+    else:
+        assert np.all(ratios > 3.0), (errs, ratios)
 
 
 # --------------------------------------------------------------------------- diffusion closed forms
@@ -209,6 +225,33 @@ def test_symmetries_commute_with_PF_and_J(sym):
     b = sym(D.jvp_full(g, Gr, q, v), affine=False)
     for c in range(4):
         assert np.max(np.abs(a[c] - b[c])) <= 1e-12 * np.max(np.abs(b[c]))
+
+
+def _reflect_y(q):
+    """The mirror image y -> 1 - y of full arrays: every field reversed along y (numpy axis 1), v negated."""
+    out = [np.flip(a, axis=1).copy() for a in q]
+    out[1] = -out[1]
+    return out
+
+
+def test_reflection_of_an_asymmetric_grid_reflects_F_and_J():
+    # y -> 1 - y maps the problem onto itself (Section 2: adiabatic y walls, buoyancy along z).  On a grid
+    # whose y faces are not symmetric the reflected field lives on the reflected grid, and F and J.v there
+    # must be the reflections of F and J.v here: every wall closure and interpolation weight of the y
+    # direction enters at both ends, so one taken from the wrong end of the axis breaks the relation
+    n = (9, 8, 7)
+    xf, yf, zf = _one_sided(n[0], 0.9), _one_sided(n[1], 1.3), _one_sided(n[2], -0.7)
+    g = D.Grid(*n, Pr=PR, xyz_faces=(xf, yf, zf))
+    gr = D.Grid(*n, Pr=PR, xyz_faces=(xf, 1.0 - yf[::-1], zf))
+    q = _rand_full(g, 41)
+    q[3] = q[3] + (1.0 - g.axes[0].xc)[None, None, :]
+    v = _rand_full(g, 42)
+    Gr = 3.0e4
+    pairs = [(D.residual_full(gr, Gr, _reflect_y(q)), _reflect_y(D.residual_full(g, Gr, q))),
+             (D.jvp_full(gr, Gr, _reflect_y(q), _reflect_y(v)), _reflect_y(D.jvp_full(g, Gr, q, v)))]
+    for a, b in pairs:
+        for c in range(4):
+            assert np.max(np.abs(a[c] - b[c])) <= 1e-12 * np.max(np.abs(b[c])), c
 
 
 def test_layout_round_trip():

@@ -29,9 +29,23 @@ def _mesh(g, which):
     return X, Y, Z
 
 
-@pytest.mark.parametrize("stretch", [0.0, 1.5])
+def _one_sided(n, a):
+    """Faces clustered towards one wall only (no mirror symmetry): x_f = (e^(a i/n) - 1) / (e^a - 1)."""
+    xf = np.expm1(a * np.arange(n + 1) / n) / np.expm1(a)
+    xf[0], xf[-1] = 0.0, 1.0
+    return xf
+
+
+def _grid(shape, stretch):
+    if stretch == "one-sided":
+        return D.Grid(*shape, xyz_faces=(_one_sided(shape[0], 1.5), _one_sided(shape[1], -1.0),
+                                         _one_sided(shape[2], 0.7)))
+    return D.Grid(*shape, stretch=stretch)
+
+
+@pytest.mark.parametrize("stretch", [0.0, 1.5, "one-sided"])
 def test_divergence_exact_on_own_axis_quadratics(stretch):
-    g = D.Grid(9, 7, 6, stretch=stretch)
+    g = _grid((9, 7, 6), stretch)
     X, Y, Z = _mesh(g, "u")
     u = X * (1 - X) * (1 + Y * Y + Z)           # zero on the x-walls, quadratic in x
     X, Y, Z = _mesh(g, "v")
@@ -46,8 +60,9 @@ def test_divergence_exact_on_own_axis_quadratics(stretch):
     assert np.max(np.abs(D.divergence_full(g, [u, v, w]) - exact)) <= 1e-12
 
 
-def test_gradient_exact_on_linear_and_uniform_quadratic():
-    g = D.Grid(8, 6, 5, stretch=1.5)
+@pytest.mark.parametrize("stretch", [1.5, "one-sided"])
+def test_gradient_exact_on_linear_and_uniform_quadratic(stretch):
+    g = _grid((8, 6, 5), stretch)
     X, Y, Z = _mesh(g, "c")
     G = D.gradient_full(g, 2.0 * X - 3.0 * Y + 0.5 * Z)
     assert np.allclose(G[0][:, :, 1:-1], 2.0, rtol=1e-12)
