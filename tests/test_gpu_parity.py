@@ -138,6 +138,45 @@ def test_jvp_project_fused(fv, shape, stretch, sigma):
     assert rel(host(out32, og.shape), ref) <= TOL32_PROJ
 
 
+def _one_sided(n, a):
+    """Caller faces clustered towards one wall only (no mirror symmetry): (e^(a i/n) - 1) / (e^a - 1)."""
+    xf = np.expm1(a * np.arange(n + 1) / n) / np.expm1(a)
+    xf[0], xf[-1] = 0.0, 1.0
+    return xf
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 64), (17, 13, 11)])
+def test_caller_faces_without_mirror_symmetry(fv, shape):
+    """Grids built from caller faces that are not mirror-symmetric, against the oracle on the same faces:
+    the FP64 fused J.v + projection (bound as for the 256-point axis: summation-order round-off amplified by
+    the smallest centre spacing) and the FP32 projection.  (64, 32, 64) has tensor-core sizes: its FP32
+    solve must take the CUDA-core passes, since the half-size eigenproblem split needs a symmetric axis."""
+    faces = (_one_sided(shape[0], 1.2), _one_sided(shape[1], -0.8), _one_sided(shape[2], 0.6))
+    og = D.Grid(*shape, Pr=PR, xyz_faces=faces)
+    g = fv.Grid(*shape, Pr=PR, faces=faces)
+    q, v = state(og, 12), vector(og, 13)
+    Gr = 1.0e5
+    P = Projector(og)
+    qf, vf = D.from_api(og, q), D.from_api(og, v)
+    J = D.jvp_full(og, Gr, qf, vf)
+    ref = D.to_api(og, P.full(J))
+    scale = D.to_api(og, J)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    fv.fv_jvp_project(g, fv.FV_FP64, Gr, 0.0, dev(q, torch.float64), dev(v, torch.float64), out)
+    got = host(out, og.shape)
+    err = max(float(np.max(np.abs(got[c] - ref[c]))) / max(float(np.max(np.abs(scale[c]))),
+                                                             float(np.max(np.abs(ref[c]))), 1e-300)
+              for c in range(4))
+    dcmin = min(float(np.min(a.dc)) for a in og.axes)
+    assert err <= max(TOL64, np.finfo(np.float64).eps * np.sqrt(max(shape)) / dcmin), err
+    v32 = round32(v)
+    ref32 = P.api(v32)
+    t32 = dev(v32, torch.float32)
+    _, div = fv.fv_project(g, fv.FV_FP32, t32, max_it=1, want_div=True)
+    assert div <= 1e-4
+    assert rel(host(t32, og.shape), ref32) <= TOL32_PROJ
+
+
 def test_dot_axpby_deterministic(fv):
     shape = (33, 17, 9)
     og = D.Grid(*shape)
