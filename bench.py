@@ -428,11 +428,12 @@ def finish(args, ws, rank, n, value, K, W, ms_step, e2e, launches, roof, hbm_ste
     }
     g.close()
     torch.cuda.empty_cache()
-    if rank == 0 and not args.no_eigen:
+    # single-GPU legs: rank 0 of the one-GPU run only (the scaling runs time the step alone)
+    if rank == 0 and ws == 1 and not args.no_eigen:
         result["time_to_eigenpair"] = eigen_leg(fv, device, n=args.eigen_grid)
-    if rank == 0 and not args.no_batch:
+    if rank == 0 and ws == 1 and not args.no_batch:
         result["batched"] = batch_leg(fv, device)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(n)
     return result
 
