@@ -8,7 +8,9 @@ J.v + projection per step.  Inputs (base state q, Krylov vectors) are seeded syn
 paper's workload shape; every buffer (268 MB per FP32 vector) is larger than the 129 MB L2.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (the reference
-arm: there is no reference code, only the paper).
+arm: there is no reference code, only the paper).  The one-GPU run also measures the time to the leading
+eigenpairs at 64^3, Gr = 4e7, mixed against plain FP64 (about ten minutes of the run, most of it the FP64
+form; --no-eigen skips it), a batched leg and the CPU baseline.
 """
 from __future__ import annotations
 
