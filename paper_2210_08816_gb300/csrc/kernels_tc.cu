@@ -686,6 +686,8 @@ bool tc_eligible(const fv_grid_s* g) {
   return encoder() != nullptr;
 }
 
+// Builds the passes' operands on the host (tc_host_operands), uploads them into one device buffer,
+// encodes the tensor maps of the B matrices and sets the kernels' shared-memory limits.
 int tc_setup(fv_grid_s* g, const std::vector<double>* idx, const std::vector<double>* idc) {
   static_assert(kTcBK == kTcSlabCols, "the host operand layout and the kernels share the K slab width");
   const int ns[3] = {g->nx, g->ny, g->nz};
